@@ -1,0 +1,337 @@
+"""Pins of the oracle's physics functions against closed forms, identities,
+textbook values and independent numerical integration (CPU only).
+
+Each check compares two *different* computations (e.g. a closed-form total
+against the quadrature of the differential cross section, or a stopping power
+against an identity that involves another cross section), so that a dropped
+term, wrong sign or swapped operand in either one shows up.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+from oracle import oracle as O
+from paper_0910_0329_gb300 import workloads as W
+
+MC2 = 0.51099895
+RE = 2.8179403262e-13
+NA = 6.02214076e23
+PARAMS = W.DEFAULT_PARAMS
+
+
+@pytest.fixture(scope="module")
+def L():
+    return O.lib()
+
+
+def M(md):
+    return O.material(md)
+
+
+WATER, BONE = M(W.WATER), M(W.BONE)
+
+
+def quad(f, a, b, **kw):
+    v, err = integrate.quad(f, a, b, epsabs=0, epsrel=1e-12, limit=400, **kw)
+    return v
+
+
+# --------------------------------------------------------------------------
+# quadrature
+# --------------------------------------------------------------------------
+def test_gauss_legendre_exact_to_degree_31(L):
+    for k in range(0, 32):
+        a, b = -0.3, 1.7
+        exact = (b ** (k + 1) - a ** (k + 1)) / (k + 1)
+        assert L.or_gl_integrate_test(k, a, b) == pytest.approx(exact, rel=1e-12, abs=1e-13)
+
+
+# --------------------------------------------------------------------------
+# photons
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("E", [0.05, 0.1, 0.511, 1.0, 6.0, 20.0])
+def test_kn_total_equals_integral_of_differential(L, E):
+    k = E / MC2
+    e0 = 1 / (1 + 2 * k)
+    num = quad(lambda e: L.or_kn_dsde(E, e), e0, 1.0)
+    assert L.or_kn_sigma(E) == pytest.approx(num, rel=1e-10)
+
+
+def test_kn_thomson_limit(L):
+    # numerically stable route (integral of the differential form) at k -> 0:
+    # sigma -> sigma_T (1 - 2k + 26/5 k^2 ...)
+    E = 1e-4
+    k = E / MC2
+    e0 = 1 / (1 + 2 * k)
+    num = quad(lambda e: L.or_kn_dsde(E, e), e0, 1.0)
+    sig_t = 8 * math.pi * RE ** 2 / 3
+    assert num == pytest.approx(sig_t * (1 - 2 * k + 5.2 * k * k), rel=1e-7)
+
+
+@pytest.mark.parametrize("E", [0.06, 0.5, 2.0, 6.0])
+def test_kn_cdf_matches_quadrature(L, E):
+    k = E / MC2
+    e0 = 1 / (1 + 2 * k)
+    tot = quad(lambda e: L.or_kn_dsde(E, e), e0, 1.0)
+    for eps in np.linspace(e0, 1.0, 7)[1:-1]:
+        part = quad(lambda e: L.or_kn_dsde(E, e), e0, eps)
+        assert L.or_kn_cdf(E, eps) == pytest.approx(part / tot, rel=1e-9)
+
+
+def test_compton_water_textbook(L):
+    # free-electron Compton coefficient of water at 1 MeV: 0.0707 cm^2/g
+    # (NIST XCOM incoherent scattering, where binding is negligible)
+    assert L.or_mu_compton(WATER, 1.0) == pytest.approx(0.0707, rel=5e-3)
+
+
+def test_photoelectric_definition_and_scaling(L):
+    c = PARAMS["c_pe"]
+    # c_pe is defined by mu_pe = mu_C in water at 30 keV
+    assert L.or_mu_photo(WATER, 0.03, c) == pytest.approx(L.or_mu_compton(WATER, 0.03), rel=1e-9)
+    # E^-3 law
+    assert L.or_mu_photo(WATER, 0.1, c) / L.or_mu_photo(WATER, 0.2, c) == pytest.approx(8.0, rel=1e-12)
+    # Z^4/A law: pseudo-element bone vs water
+    zbone = 13.8 ** 4 / (13.8 / 0.5148)
+    zw = W.WATER["elements"][0][2] / 1.008 + W.WATER["elements"][1][2] * 8 ** 4 / 15.999
+    assert L.or_mu_photo(BONE, 0.1, c) / L.or_mu_photo(WATER, 0.1, c) == pytest.approx(zbone / zw, rel=1e-12)
+
+
+@pytest.mark.parametrize("kappa", [10.0, 50.0, 1000.0])
+def test_pair_full_range_closed_form(L, kappa):
+    # 4 * int_0^1 [e^2+(1-e)^2+2/3 e(1-e)] (ln(2k e(1-e)) - 1/2) de = 28/9 ln(2k) - 218/27
+    exact = 28.0 / 9.0 * math.log(2 * kappa) - 218.0 / 27.0
+    assert L.or_pair_integral(kappa, 0.0, 1.0, 0) == pytest.approx(exact, rel=1e-9)
+
+
+def test_pair_physical_integral_limits(L):
+    # kinematic + positivity truncation vanishes relative to the total as k grows
+    for kappa in [1e4, 1e5]:
+        full = 28.0 / 9.0 * math.log(2 * kappa) - 218.0 / 27.0
+        phys = L.or_pair_integral(kappa, 1 / kappa, 1 - 1 / kappa, 1)
+        assert abs(phys / full - 1) < 20 * math.log(kappa) / kappa
+    # the physical integral of the clamped shape agrees with scipy on the same support
+    kappa = 12.0
+    phys = L.or_pair_integral(kappa, 1 / kappa, 1 - 1 / kappa, 1)
+    num = 4 * quad(lambda e: L.or_pair_dsde_shape(kappa, e, 1), 1 / kappa, 1 - 1 / kappa, points=[0.5])
+    assert phys == pytest.approx(num, rel=1e-8)
+
+
+def test_pair_threshold(L):
+    # the clamped model switches on where ln(k/2) = 1/2, i.e. k = 2 e^{1/2}
+    kth = 2 * math.exp(0.5)
+    assert L.or_mu_pair(WATER, 0.999 * kth * MC2) == 0.0
+    assert L.or_mu_pair(WATER, 1.05 * kth * MC2) > 0.0
+    assert L.or_mu_pair(WATER, 1.0) == 0.0
+
+
+# --------------------------------------------------------------------------
+# electrons
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("T", [1.0, 5.0, 20.0])
+def test_restricted_plus_hard_moller_equals_unrestricted(L, T):
+    wcc = PARAMS["wcc"]
+    hard = quad(lambda w: w * L.or_moller_dsdw(WATER, T, w), wcc, T / 2)
+    unrestricted = L.or_scol(WATER, T, T)  # cut >= T/2 selects the unrestricted form
+    assert L.or_scol(WATER, T, wcc) + hard == pytest.approx(unrestricted, rel=1e-10)
+
+
+def test_restricted_collision_continuous_at_double_cut(L):
+    wcc = PARAMS["wcc"]
+    a = L.or_scol(WATER, 2 * wcc * (1 - 1e-9), wcc)
+    b = L.or_scol(WATER, 2 * wcc * (1 + 1e-9), wcc)
+    assert a == pytest.approx(b, rel=1e-6)
+
+
+def test_water_collision_stopping_power_textbook(L):
+    # ESTAR, water, 1 MeV: collision stopping power 1.849 MeV cm^2/g; the model
+    # has no density-effect correction, which makes it slightly high
+    v = L.or_scol(WATER, 1.0, 1.0)
+    assert 1.849 <= v <= 1.849 * 1.03
+
+
+def test_radiation_length_textbook(L):
+    # Dahl's fit reproduces the tabulated radiation length of water, 36.08 g/cm^2, to ~1 %
+    assert L.or_x0(WATER) == pytest.approx(36.08, rel=0.01)
+
+
+@pytest.mark.parametrize("T", [0.3, 2.0, 20.0])
+def test_brems_stopping_and_cross_section_vs_spectrum(L, T):
+    wcr = PARAMS["wcr"]
+    num_sp = quad(lambda k: k * L.or_brems_dsdk(WATER, T, k), 0.0, min(wcr, T))
+    assert L.or_srad(WATER, T, wcr) == pytest.approx(num_sp, rel=1e-10)
+    num_sig = quad(lambda k: L.or_brems_dsdk(WATER, T, k), wcr, T)
+    assert L.or_brems_sigma(WATER, T, wcr) == pytest.approx(num_sig, rel=1e-10)
+
+
+def test_radiative_stopping_high_energy_limit(L):
+    # full radiative stopping power (cut at T) tends to E / X0
+    T = 1e4
+    assert L.or_srad(WATER, T, T) / ((T + MC2) / L.or_x0(WATER)) == pytest.approx(1.0, abs=1e-4)
+
+
+@pytest.mark.parametrize("T", [0.45, 1.0, 20.0])
+def test_moller_total_vs_differential(L, T):
+    wcc = PARAMS["wcc"]
+    num = quad(lambda w: L.or_moller_dsdw(WATER, T, w), wcc, T / 2)
+    assert L.or_moller_sigma(WATER, T, wcc) == pytest.approx(num, rel=1e-10)
+    assert L.or_moller_sigma(WATER, 2 * wcc * 0.999, wcc) == 0.0
+
+
+def test_hard_cross_sections_increase_with_energy(L):
+    # the delta-scattering majorant of the electron step relies on this
+    Ts = np.geomspace(0.2, 21.0, 400)
+    for m in (WATER, BONE):
+        s = np.array([L.or_moller_sigma(m, t, PARAMS["wcc"]) + L.or_brems_sigma(m, t, PARAMS["wcr"]) for t in Ts])
+        assert (np.diff(s) >= 0).all()
+
+
+def test_lambda1_bracket_is_transport_integral(L):
+    # the bracket ln(1+1/eta) - 1/(1+eta) is the integral of (1-mu)/(1-mu+2eta)^2 dmu;
+    # check that lambda1^-1 equals 2 pi n Z(Z+1) re^2/(beta^4 gamma^2) times that integral
+    T = 2.0
+    t = T / MC2
+    g = t + 1
+    b2 = 1 - 1 / g ** 2
+    bg2 = t * (t + 2)
+    alpha = 1 / 137.035999084
+    tot = 0.0
+    for Z, A, w in W.WATER["elements"]:
+        eta = 0.25 * (alpha * Z ** (1 / 3) / 0.885) ** 2 / bg2 * (1.13 + 3.76 * (alpha * Z) ** 2 / b2)
+        integ = quad(lambda mu: (1 - mu) / (1 - mu + 2 * eta) ** 2, -1, 1, points=[1 - 1e-3, 1 - 1e-5])
+        tot += NA * w / A * 2 * math.pi * Z * (Z + 1) * RE ** 2 / (b2 * bg2) * integ
+    assert L.or_lambda1_inv(WATER, T) == pytest.approx(tot, rel=1e-8)
+
+
+def test_csda_path_vs_scipy(L):
+    p = O.params(PARAMS)
+    S = lambda T: L.or_scol(WATER, T, PARAMS["wcc"]) + L.or_srad(WATER, T, PARAMS["wcr"])
+    for lo, hi in [(0.2, 0.21), (0.2, 20.0), (5.0, 5.25), (0.3, 0.5), (0.04, 0.3)]:
+        pts = [x for x in (PARAMS["wcr"], 2 * PARAMS["wcc"]) if lo < x < hi]
+        num = quad(lambda T: 1.0 / S(T), lo, hi, points=pts or None)
+        assert L.or_csda_path(WATER, p, lo, hi) == pytest.approx(num, rel=1e-10)
+
+
+def test_csda_energy_inverts_path_and_is_additive(L):
+    p = O.params(PARAMS)
+    for T, s in [(20.0, 0.9), (1.0, 0.02), (0.25, 0.01)]:
+        Tp = L.or_csda_energy(WATER, p, T, s)
+        assert L.or_csda_path(WATER, p, Tp, T) == pytest.approx(s, rel=1e-11)
+    a, b, c = 0.3, 2.0, 15.0
+    assert L.or_csda_path(WATER, p, a, c) == pytest.approx(
+        L.or_csda_path(WATER, p, a, b) + L.or_csda_path(WATER, p, b, c), rel=1e-12)
+
+
+def test_msc_inverse_and_mean(L):
+    for q in np.concatenate([np.geomspace(1e-9, 0.5, 25), 1 - np.geomspace(1e-8, 0.4, 12)]):
+        A = L.or_msc_A(q)
+        assert L.or_msc_mean(A) == pytest.approx(q, rel=1e-10)
+    for A in [1e-6, 1e-3, 0.1, 2.0, 50.0]:
+        p = lambda x: 2 * A * (1 + A) / (x + 2 * A) ** 2
+        assert quad(p, 0, 2, points=[A, 10 * A]) == pytest.approx(1.0, rel=1e-10)
+        assert L.or_msc_mean(A) == pytest.approx(quad(lambda x: x * p(x), 0, 2, points=[A, 10 * A]), rel=1e-9)
+
+
+def test_spectrum_cdf_vs_quadrature(L):
+    f = lambda E: (1 - E / 6) / math.sqrt(E)
+    Z = quad(f, 0.25, 6.0)
+    assert Z == pytest.approx(4.0 / 3.0 * math.sqrt(6.0) - 1.0 + 1.0 / 72.0, rel=1e-12)
+    for E in [0.3, 1.0, 2.5, 5.9]:
+        assert L.or_spectrum_cdf(E) == pytest.approx(quad(f, 0.25, E) / Z, rel=1e-11)
+    mean = quad(lambda E: E * f(E), 0.25, 6.0) / Z
+    assert mean == pytest.approx(1.6834, abs=2e-4)
+
+
+# --------------------------------------------------------------------------
+# samplers: chi^2 against the binned differential forms (fixed seeds)
+# --------------------------------------------------------------------------
+def chi2_p(samples, edges, probs):
+    cnt, _ = np.histogram(samples, edges)
+    exp = probs / probs.sum() * len(samples)
+    keep = exp > 5
+    chi = ((cnt[keep] - exp[keep]) ** 2 / exp[keep]).sum()
+    return stats.chi2.sf(chi, keep.sum() - 1)
+
+
+@pytest.mark.parametrize("E", [0.1, 1.0, 6.0])
+def test_kn_sampler_chi2(L, E):
+    k = E / MC2
+    e0 = 1 / (1 + 2 * k)
+    s = O.sample(O.S_KN, E, 0, 200000, seed=11)
+    assert s.min() >= e0 and s.max() <= 1.0
+    edges = np.linspace(e0, 1.0, 41)
+    probs = np.array([quad(lambda e: L.or_kn_dsde(E, e), a, b) for a, b in zip(edges[:-1], edges[1:])])
+    assert chi2_p(s, edges, probs) > 0.01
+
+
+@pytest.mark.parametrize("T", [0.5, 3.0, 20.0])
+def test_moller_sampler_chi2(L, T):
+    wcc = PARAMS["wcc"]
+    s = O.sample(O.S_MOLLER, T, wcc, 200000, seed=12) * T
+    assert s.min() >= wcc * (1 - 1e-12) and s.max() <= T / 2 * (1 + 1e-12)
+    edges = np.geomspace(wcc, T / 2, 31)
+    probs = np.array([quad(lambda w: L.or_moller_dsdw(WATER, T, w), a, b) for a, b in zip(edges[:-1], edges[1:])])
+    assert chi2_p(s, edges, probs) > 0.01
+
+
+@pytest.mark.parametrize("T", [0.3, 5.0, 20.0])
+def test_brems_sampler_chi2(L, T):
+    wcr = PARAMS["wcr"]
+    s = O.sample(O.S_BREMS, T, wcr, 200000, seed=13)
+    edges = np.geomspace(wcr, T, 31)
+    probs = np.array([quad(lambda k: L.or_brems_dsdk(WATER, T, k), a, b) for a, b in zip(edges[:-1], edges[1:])])
+    assert chi2_p(s, edges, probs) > 0.01
+
+
+@pytest.mark.parametrize("E", [2.0, 6.0, 20.0])
+def test_pair_sampler_chi2(L, E):
+    k = E / MC2
+    s = O.sample(O.S_PAIR, E, 0, 200000, seed=14)
+    edges = np.linspace(1 / k, 1 - 1 / k, 31)
+    probs = np.array([quad(lambda e: L.or_pair_dsde_shape(k, e, 1), a, b) for a, b in zip(edges[:-1], edges[1:])])
+    assert chi2_p(s, edges, probs) > 0.01
+
+
+@pytest.mark.parametrize("A", [1e-4, 0.05, 3.0])
+def test_msc_sampler_mean_and_shape(L, A):
+    s = O.sample(O.S_MSC, A, 0, 200000, seed=15)
+    target = L.or_msc_mean(A)
+    assert abs(s.mean() - target) < 4 * s.std() / math.sqrt(len(s))
+    edges = np.concatenate([[0], np.geomspace(A * 1e-2, 2, 30)])
+    cdf = lambda x: (1 + A) * x / (x + 2 * A)
+    probs = np.diff(cdf(edges))
+    assert chi2_p(s, edges, probs) > 0.01
+
+
+def test_msc_isotropic_limit(L):
+    s = O.sample(O.S_MSC, 1e9, 0, 100000, seed=16)
+    assert stats.kstest(s / 2.0, "uniform").pvalue > 0.01
+
+
+def test_spectrum_sampler(L):
+    s = O.sample(O.S_SPECTRUM, 0, 0, 200000, seed=17)
+    assert s.min() >= 0.25 and s.max() <= 6.0
+    assert abs(s.mean() - 1.6834) < 4 * s.std() / math.sqrt(len(s))
+    edges = np.linspace(0.25, 6.0, 41)
+    probs = np.diff([L.or_spectrum_cdf(e) for e in edges])
+    assert chi2_p(s, edges, probs) > 0.01
+
+
+# --------------------------------------------------------------------------
+# RANECU
+# --------------------------------------------------------------------------
+def test_ranecu_matches_direct_modular_arithmetic():
+    s1, s2 = 12345, 67890
+    u, (e1, e2) = O.ranecu_stream(s1, s2, 5000)
+    a1, m1, a2, m2 = 40014, 2147483563, 40692, 2147483399
+    x1, x2 = s1, s2
+    for i in range(5000):
+        x1 = (a1 * x1) % m1
+        x2 = (a2 * x2) % m2
+        z = x1 - x2
+        if z < 1:
+            z += m1 - 1
+        assert u[i] == pytest.approx(z / m1, rel=1e-15)
+    assert (e1, e2) == (x1, x2)
+    assert stats.kstest(u, "uniform").pvalue > 0.01
