@@ -1,0 +1,177 @@
+/*
+ * dpm.h -- C ABI of the GB300 coupled electron-photon Monte Carlo dose library.
+ *
+ * Method: Jia et al., "Development of a GPU-based Monte Carlo dose calculation
+ * code for coupled electron-photon transport" (arXiv:0910.0329):
+ *   Sec. 2.1  DPM transport scheme (condensed-history electrons with CSDA below
+ *             the cuts and detailed Moller/bremsstrahlung above them, random
+ *             hinge elastic deflections, Woodcock photon tracking);
+ *   Sec. 2.2  the run: load data, transport N histories (each source particle
+ *             with all its secondaries), read the dose back;
+ *   Sec. 2.3  single-precision transport arithmetic;
+ *   Sec. 2.4  per-voxel dose accumulation with atomic adds; per-thread RNG;
+ *   Sec. 3    point source, field at SAD, absorption energies, sigma_D.
+ *
+ * Conventions for every call:
+ *   - returns a dpm_status code (0 = success); no exceptions cross the ABI;
+ *     dpm_last_error() gives a message for the last failing call on a context;
+ *   - host pointers are owned by the caller and only read (or written, for
+ *     outputs) during the call; the context owns every device allocation it
+ *     makes and frees it in dpm_destroy();
+ *   - work is queued on the context's stream (dpm_set_stream, default: a
+ *     stream the context creates); dpm_run() is asynchronous, dpm_read_dose()
+ *     and dpm_sync() synchronise and report device-side errors;
+ *   - phantom layout: voxel v = i + nx*(j + ny*k); the phantom occupies
+ *     [0,nx*dx] x [0,ny*dy] x [0,nz*dz] cm; mat[v] indexes the material list
+ *     given to dpm_build_tables(); rho[v] is the mass density in g/cm^3.
+ * Units: MeV, cm, g/cm^3.
+ */
+#ifndef DPM_H
+#define DPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dpm_ctx dpm_ctx;
+
+typedef enum {
+    DPM_OK = 0,
+    DPM_EINVAL = -1,          /* bad argument (null pointer, size, range) */
+    DPM_ENOMEM = -2,          /* device allocation failed */
+    DPM_ECUDA = -3,           /* a CUDA runtime call failed (message has the CUDA error) */
+    DPM_EQUEUE_OVERFLOW = -4, /* a particle queue or stack overflowed: rerun with larger capacity */
+    DPM_ETIMEOUT = -5,        /* a bounded device wait gave up */
+    DPM_ESTATE = -6           /* call out of order (e.g. run before tables) */
+} dpm_status;
+
+#define DPM_MAX_ELEM 8
+#define DPM_MAX_MAT 16
+
+/* A material: elements (atomic number Z, molar mass A in g/mol, mass fraction
+   w) and mean excitation energy I in eV. */
+typedef struct {
+    int n_elem;
+    double Z[DPM_MAX_ELEM], A[DPM_MAX_ELEM], w[DPM_MAX_ELEM];
+    double i_ev;
+} dpm_material;
+
+/* Transport and table parameters (Sec. 3 absorption energies; the cuts and
+   step parameter of the condensed-history scheme of Sec. 2.1). */
+typedef struct {
+    double eabs_e;  /* electron absorption energy (MeV) */
+    double eabs_g;  /* photon absorption energy (MeV) */
+    double wcc;     /* Moller hard-collision cut (MeV) */
+    double wcr;     /* bremsstrahlung hard-emission cut (MeV) */
+    double f_e;     /* maximum fractional CSDA energy loss per electron step */
+    double c_pe;    /* photoelectric strength: mu_pe/rho = c_pe sum(w Z^4/A) / E^3 */
+    double e_max;   /* highest particle energy the tables must cover (MeV) */
+    int n_e;        /* energy nodes of the per-material tables (>= 64) */
+} dpm_table_params;
+
+/* Beam (Sec. 3): point source at distance `sad` from the isocentre `iso`;
+   the fx x fy field lies in the isocentre plane normal to the beam axis;
+   gantry_deg rotates the beam about the y axis through the isocentre
+   (0 = travelling along +z). */
+typedef struct {
+    int particle;   /* 0 photon, 1 electron */
+    int spectrum;   /* 0 monoenergetic at `energy`, 1 synthetic 6 MV (1-E/6)E^-1/2 on [0.25,6] MeV */
+    double energy;
+    double iso[3];
+    double sad, fx, fy, gantry_deg;
+} dpm_source;
+
+/* Kernel selection and launch shape.  Zero fields take defaults. */
+enum { DPM_KERNEL_QUEUE = 0, DPM_KERNEL_HISTORY = 1 };
+typedef struct {
+    int kernel;        /* DPM_KERNEL_QUEUE (persistent, particle queues) or
+                          DPM_KERNEL_HISTORY (one history per thread, private stack) */
+    int n_batches;     /* history batches for the sigma estimate (default 50, max 1024) */
+    int block_size;    /* threads per block (multiple of 32) */
+    int blocks_per_sm; /* resident blocks per SM for the persistent kernel */
+    int queue_log2;    /* log2 of each particle queue's capacity */
+    int refill_min;    /* lanes that must be idle before a warp refills */
+    double timeout_s;  /* bound on any device wait (default 20 s) */
+} dpm_run_opts;
+
+/* Run summary returned by dpm_read_dose(). Energies in MeV. */
+typedef struct {
+    uint64_t n_histories;
+    int32_t n_batches;
+    int32_t error_flags;          /* bit 0 stack/queue overflow, bit 1 step cap, bit 2 timeout */
+    double emitted, deposited, escaped, missed;
+    uint64_t n_e_steps, n_g_flights, n_g_interactions;
+    uint64_t n_tally_atomics;     /* 64-bit atomic adds issued to the tally */
+    uint64_t n_pushed;            /* secondaries created */
+} dpm_run_stats;
+
+int dpm_create(dpm_ctx **out, int cuda_device);
+void dpm_destroy(dpm_ctx *ctx);
+const char *dpm_last_error(const dpm_ctx *ctx);
+
+/* Use an external CUDA stream (cudaStream_t passed as void*); NULL restores
+   the context's own stream. */
+int dpm_set_stream(dpm_ctx *ctx, void *cuda_stream);
+
+/* Copy a voxel phantom (host arrays, nx*ny*nz entries) to the device.  Sizes
+   up to 2047 x 2047 x 1023 voxels.  Returns its id in *phantom_id. */
+int dpm_load_phantom(dpm_ctx *ctx, int nx, int ny, int nz, double dx, double dy, double dz,
+                     const uint8_t *mat, const float *rho, int *phantom_id);
+int dpm_free_phantom(dpm_ctx *ctx, int phantom_id);
+
+/* Build the FP32 device tables (per-material attenuation, range, stopping
+   power, hard cross sections, transport mean free path; inverse-CDF sampling
+   tables) from FP64 closed forms of the model.  Must precede dpm_run(). */
+int dpm_build_tables(dpm_ctx *ctx, const dpm_material *mats, int n_mat, const dpm_table_params *p);
+
+/* Transport histories [first_history, first_history + n_histories) from
+   `src` into the phantom's tally (Sec. 2.2).  Random numbers are keyed by
+   (seed, history id, particle id), so the tally does not depend on launch
+   shape, and splitting a history range over several calls adds up to the
+   same integer tally.  Asynchronous on the context stream. */
+int dpm_run(dpm_ctx *ctx, int phantom_id, const dpm_source *src, uint64_t first_history,
+            uint64_t n_histories, uint64_t seed, const dpm_run_opts *opts);
+
+/* Zero the phantom's accumulated tally and statistics. */
+int dpm_reset_tally(dpm_ctx *ctx, int phantom_id);
+
+/* Synchronise and read the accumulated result.  dose_gy and sigma_gy (Gy per
+   history, sigma of the mean by the batch method) and s1_raw (integer tally,
+   units of 2^-32 MeV) are caller-allocated host arrays of nx*ny*nz entries;
+   any of them may be NULL.  stats may be NULL. */
+int dpm_read_dose(dpm_ctx *ctx, int phantom_id, double *dose_gy, double *sigma_gy, int64_t *s1_raw,
+                  dpm_run_stats *stats);
+
+/* Same, writing dose and sigma into caller-allocated *device* arrays. */
+int dpm_read_dose_device(dpm_ctx *ctx, int phantom_id, double *d_dose_gy, double *d_sigma_gy,
+                         dpm_run_stats *stats);
+
+/* Wait for queued work; reports device-side errors of earlier runs. */
+int dpm_sync(dpm_ctx *ctx);
+
+/* ---- diagnostics used by the parity tests ------------------------------ */
+
+/* Evaluate the device tables at n energies (host arrays).  which: 0 mu/rho
+   total (cm^2/g), 1 Compton fraction, 2 photoelectric fraction, 3 range
+   R(T) from the lowest table energy (g/cm^2), 4 stopping power (MeV cm^2/g),
+   5 hard cross section (cm^2/g), 6 inverse transport mfp (cm^2/g), 7 Moller
+   fraction of the hard cross section, 8 CSDA energy after mass path
+   aux[i] starting from energy[i], 9 majorant mu_max of phantom `mat`
+   (1/cm, `mat` is then the phantom id). */
+int dpm_diag_table(dpm_ctx *ctx, int which, int mat, int n, const double *energy, const double *aux, double *out);
+
+/* Run the device samplers on n uniforms u[i] (host) at energy e (MeV):
+   which 0 KN eps, 1 Moller eps = W/T, 2 brems k (MeV), 3 pair eps,
+   4 MSC 1-mu for q = aux (mean of 1-mu), 5 6 MV spectrum energy. */
+int dpm_diag_sample(dpm_ctx *ctx, int which, double e, double aux, int n, const double *u, double *out);
+
+/* n Philox4x32-10 blocks for counters ctr[4*i..] and keys key[2*i..] (host). */
+int dpm_diag_philox(dpm_ctx *ctx, int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -956,6 +956,7 @@ int or_run(const or_phantom *ph, const or_material *mats, int n_mat, const or_pa
         }
         c->n_touched = 0;
         st->deposited += c->h_dep;
+        st->deposited2 += c->h_dep * c->h_dep;
         st->escaped += c->h_esc;
         double rel = fabs(emitted - c->h_dep - c->h_esc) / emitted;
         if (rel > st->max_balance_rel) st->max_balance_rel = rel;

@@ -64,6 +64,7 @@ typedef struct {
 typedef struct {
     double emitted, deposited, escaped, missed;
     double max_balance_rel;          /* max over histories |emit-dep-esc-miss|/emit */
+    double deposited2;               /* sum over histories of (energy deposited in the history)^2 */
     double e_path;                   /* total electron path length, cm */
     long long n_hist, n_missed;
     long long n_e_steps, n_g_interactions, n_g_voxel_steps;

@@ -61,7 +61,7 @@ class SourceS(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("emitted", C.c_double), ("deposited", C.c_double), ("escaped", C.c_double), ("missed", C.c_double),
-                ("max_balance_rel", C.c_double), ("e_path", C.c_double), ("n_hist", C.c_longlong),
+                ("max_balance_rel", C.c_double), ("deposited2", C.c_double), ("e_path", C.c_double), ("n_hist", C.c_longlong),
                 ("n_missed", C.c_longlong), ("n_e_steps", C.c_longlong), ("n_g_interactions", C.c_longlong),
                 ("n_g_voxel_steps", C.c_longlong), ("n_dep", C.c_longlong), ("n_dep_runs", C.c_longlong),
                 ("n_sec_e", C.c_longlong), ("n_sec_g", C.c_longlong), ("n_positrons", C.c_longlong)]
@@ -154,6 +154,14 @@ class OracleResult:
 
     def mean_energy(self):
         return self.S1 / self.n
+
+    def total_energy_and_sigma(self):
+        """Mean energy deposited per history in the whole phantom and its
+        standard error (history by history)."""
+        n = self.n
+        m = self.stats["deposited"] / n
+        var = max(self.stats["deposited2"] / n - m * m, 0.0)
+        return m, math.sqrt(var / max(n - 1, 1))
 
     def sigma_mean_energy(self):
         """Standard error of the per-history mean energy, history by history."""

@@ -1,0 +1,547 @@
+// dpm_capi.cu -- the C ABI declared in include/dpm.h: context, device memory,
+// phantom upload, table upload, run orchestration (zero slabs -> transport ->
+// fold) and result read-back.  The run sequence follows Sec. 2.2: data are
+// loaded once, histories are transported in launches, and the dose is copied
+// back at the end.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dpm_internal.h"
+#include "dpm_kernels.h"
+#include "dpm_queue.h"
+
+using namespace dpm;
+
+namespace {
+
+struct PhantomState {
+  int nx = 0, ny = 0, nz = 0;
+  double dx = 0, dy = 0, dz = 0;
+  size_t V = 0;
+  uint8_t *d_mat = nullptr;
+  float *d_rho = nullptr;
+  float *d_mumax = nullptr;
+  int mumax_version = -1;
+  int max_mat = 0;
+  double rho_max[DPM_MAX_MAT] = {0};
+  unsigned long long *d_slabs = nullptr;
+  size_t slab_batches = 0;
+  long long *d_S1 = nullptr;
+  double *d_Q = nullptr;
+  unsigned long long *d_counters = nullptr;
+  double *d_inv_nb = nullptr;
+  double *d_dose = nullptr, *d_sigma = nullptr;
+  uint64_t n_total = 0;
+  uint64_t b_total = 0;
+};
+
+}  // namespace
+
+struct dpm_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t own = nullptr, stream = nullptr;
+  std::string err;
+  bool tables_ready = false;
+  int tables_version = 0;
+  dpm_table_params params{};
+  HostTables ht;
+  DevTables dt{};
+  std::vector<void *> table_mem;
+  std::vector<std::unique_ptr<PhantomState>> phantoms;
+  int *d_err = nullptr;
+  QueueState queue;
+};
+
+namespace {
+
+int fail(dpm_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                              \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail(ctx, DPM_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+int dalloc(dpm_ctx *c, T **p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(c, DPM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return DPM_OK;
+}
+
+void free_phantom(PhantomState *p) {
+  if (!p) return;
+  cudaFree(p->d_mat);
+  cudaFree(p->d_rho);
+  cudaFree(p->d_mumax);
+  cudaFree(p->d_slabs);
+  cudaFree(p->d_S1);
+  cudaFree(p->d_Q);
+  cudaFree(p->d_counters);
+  cudaFree(p->d_inv_nb);
+  cudaFree(p->d_dose);
+  cudaFree(p->d_sigma);
+}
+
+void free_tables(dpm_ctx *c) {
+  for (void *p : c->table_mem) cudaFree(p);
+  c->table_mem.clear();
+  c->tables_ready = false;
+}
+
+PhantomState *get_phantom(dpm_ctx *c, int id) {
+  if (id < 0 || id >= int(c->phantoms.size())) return nullptr;
+  return c->phantoms[id].get();
+}
+
+template <class T>
+int upload(dpm_ctx *c, const std::vector<T> &h, const T **out) {
+  T *d = nullptr;
+  int rc = dalloc(c, &d, h.size());
+  if (rc) return rc;
+  c->table_mem.push_back(d);
+  CUDA_TRY(c, cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *out = d;
+  return DPM_OK;
+}
+
+// Photon majorant of a phantom: for every energy node, the largest
+// rho * mu/rho over the materials present, at their largest density.
+int update_mumax(dpm_ctx *c, PhantomState *p) {
+  if (p->mumax_version == c->tables_version && p->d_mumax) return DPM_OK;
+  const HostTables &t = c->ht;
+  std::vector<float> mm(t.n_e, 0.f);
+  for (int i = 0; i < t.n_e; ++i) {
+    double best = 0;
+    for (int m = 0; m <= p->max_mat && m < t.n_mat; ++m)
+      if (p->rho_max[m] > 0) best = std::max(best, p->rho_max[m] * t.mu_mass_nodes[size_t(m) * t.n_e + i]);
+    mm[i] = float(best * (1.0 + 1e-5));
+  }
+  if (!p->d_mumax) {
+    int rc = dalloc(c, &p->d_mumax, size_t(t.n_e));
+    if (rc) return rc;
+  }
+  CUDA_TRY(c, cudaMemcpy(p->d_mumax, mm.data(), mm.size() * sizeof(float), cudaMemcpyHostToDevice));
+  p->mumax_version = c->tables_version;
+  return DPM_OK;
+}
+
+uint64_t splitmix(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+}  // namespace
+
+extern "C" {
+
+int dpm_create(dpm_ctx **out, int cuda_device) {
+  if (!out) return DPM_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || cuda_device < 0 || cuda_device >= n) {
+    cudaGetLastError();
+    return DPM_ECUDA;
+  }
+  dpm_ctx *c = new (std::nothrow) dpm_ctx();
+  if (!c) return DPM_ENOMEM;
+  c->device = cuda_device;
+  if (cudaSetDevice(cuda_device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, cuda_device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return DPM_ECUDA;
+  }
+  c->stream = c->own;
+  *out = c;
+  return DPM_OK;
+}
+
+void dpm_destroy(dpm_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto &p : c->phantoms) free_phantom(p.get());
+  free_tables(c);
+  queue_free(c->queue);
+  cudaFree(c->d_err);
+  if (c->own) cudaStreamDestroy(c->own);
+  delete c;
+}
+
+const char *dpm_last_error(const dpm_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int dpm_set_stream(dpm_ctx *c, void *s) {
+  if (!c) return DPM_EINVAL;
+  c->stream = s ? (cudaStream_t)s : c->own;
+  return DPM_OK;
+}
+
+int dpm_load_phantom(dpm_ctx *c, int nx, int ny, int nz, double dx, double dy, double dz, const uint8_t *mat,
+                     const float *rho, int *phantom_id) {
+  if (!c) return DPM_EINVAL;
+  if (!mat || !rho || !phantom_id) return fail(c, DPM_EINVAL, "null pointer");
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 2047 || ny > 2047 || nz > 1023)
+    return fail(c, DPM_EINVAL, "phantom size out of range (1..2047 x 1..2047 x 1..1023)");
+  if (!(dx > 0 && dy > 0 && dz > 0)) return fail(c, DPM_EINVAL, "voxel size must be positive");
+  cudaSetDevice(c->device);
+  auto p = std::make_unique<PhantomState>();
+  p->nx = nx; p->ny = ny; p->nz = nz;
+  p->dx = dx; p->dy = dy; p->dz = dz;
+  p->V = size_t(nx) * ny * nz;
+  for (size_t v = 0; v < p->V; ++v) {
+    if (mat[v] >= DPM_MAX_MAT) return fail(c, DPM_EINVAL, "material index >= 16");
+    if (!(rho[v] > 0.f) || !std::isfinite(rho[v])) return fail(c, DPM_EINVAL, "density must be positive and finite");
+    p->max_mat = std::max(p->max_mat, int(mat[v]));
+    p->rho_max[mat[v]] = std::max(p->rho_max[mat[v]], double(rho[v]));
+  }
+  int rc;
+  if ((rc = dalloc(c, &p->d_mat, p->V)) || (rc = dalloc(c, &p->d_rho, p->V)) || (rc = dalloc(c, &p->d_S1, p->V)) ||
+      (rc = dalloc(c, &p->d_Q, p->V)) || (rc = dalloc(c, &p->d_counters, size_t(C_N))) ||
+      (rc = dalloc(c, &p->d_inv_nb, size_t(1024)))) {
+    free_phantom(p.get());
+    return rc;
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(p->d_mat, mat, p->V, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(p->d_rho, rho, p->V * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(p->d_S1, 0, p->V * sizeof(long long), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(p->d_Q, 0, p->V * sizeof(double), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(p->d_counters, 0, C_N * sizeof(unsigned long long), c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->phantoms.push_back(std::move(p));
+  *phantom_id = int(c->phantoms.size()) - 1;
+  return DPM_OK;
+}
+
+int dpm_free_phantom(dpm_ctx *c, int id) {
+  if (!c) return DPM_EINVAL;
+  PhantomState *p = get_phantom(c, id);
+  if (!p) return fail(c, DPM_EINVAL, "bad phantom id");
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_phantom(p);
+  c->phantoms[id].reset();
+  return DPM_OK;
+}
+
+int dpm_build_tables(dpm_ctx *c, const dpm_material *mats, int n_mat, const dpm_table_params *p) {
+  if (!c) return DPM_EINVAL;
+  if (!mats || !p) return fail(c, DPM_EINVAL, "null pointer");
+  cudaSetDevice(c->device);
+  HostTables ht;
+  std::string err;
+  if (!build_tables(mats, n_mat, *p, ht, err)) return fail(c, DPM_EINVAL, err);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  free_tables(c);
+  c->ht = std::move(ht);
+  const HostTables &t = c->ht;
+  DevTables d{};
+  d.n_mat = t.n_mat;
+  d.n_e = t.n_e;
+  d.lnE_lo = float(std::log(t.e_lo));
+  d.inv_dlnE = float((t.n_e - 1) / (std::log(t.e_hi) - std::log(t.e_lo)));
+  int rc;
+  const float *ph, *el;
+  if ((rc = upload(c, t.ph, &ph)) || (rc = upload(c, t.el, &el)) || (rc = upload(c, t.pmol, &d.pmol))) return rc;
+  d.ph = reinterpret_cast<const float4 *>(ph);
+  d.el = reinterpret_cast<const float4 *>(el);
+  auto samp = [&](const std::vector<float> &v, int ne, double lo, double hi, SampTab &s) {
+    s.ne = ne;
+    s.nu = t.nu;
+    s.lnE0 = float(std::log(lo));
+    s.inv_dlnE = float((ne - 1) / (std::log(hi) - std::log(lo)));
+    return upload(c, v, &s.y);
+  };
+  if ((rc = samp(t.kn, t.kn_ne, t.kn_lo, t.kn_hi, d.kn)) || (rc = samp(t.mol, t.mol_ne, t.mol_lo, t.mol_hi, d.mol)) ||
+      (rc = samp(t.brem, t.brem_ne, t.brem_lo, t.brem_hi, d.brem)) ||
+      (rc = samp(t.pair, t.pair_ne, t.pair_lo, t.pair_hi, d.pair)) || (rc = upload(c, t.msc, &d.msc_lnA)))
+    return rc;
+  d.msc_n = t.msc_n;
+  d.msc_x0 = float(t.msc_x0);
+  d.msc_inv_dx = float((t.msc_n - 1) / (t.msc_x1 - t.msc_x0));
+  d.eabs_e = float(p->eabs_e);
+  d.eabs_g = float(p->eabs_g);
+  d.wcc = float(p->wcc);
+  d.wcr = float(p->wcr);
+  d.f_e = float(p->f_e);
+  c->dt = d;
+  c->params = *p;
+  c->tables_ready = true;
+  c->tables_version++;
+  return DPM_OK;
+}
+
+int dpm_reset_tally(dpm_ctx *c, int id) {
+  if (!c) return DPM_EINVAL;
+  PhantomState *p = get_phantom(c, id);
+  if (!p) return fail(c, DPM_EINVAL, "bad phantom id");
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaMemsetAsync(p->d_S1, 0, p->V * sizeof(long long), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(p->d_Q, 0, p->V * sizeof(double), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(p->d_counters, 0, C_N * sizeof(unsigned long long), c->stream));
+  p->n_total = 0;
+  p->b_total = 0;
+  return DPM_OK;
+}
+
+int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t n, uint64_t seed,
+            const dpm_run_opts *opts) {
+  if (!c) return DPM_EINVAL;
+  if (!src) return fail(c, DPM_EINVAL, "null source");
+  if (!c->tables_ready) return fail(c, DPM_ESTATE, "dpm_build_tables() must precede dpm_run()");
+  PhantomState *p = get_phantom(c, id);
+  if (!p) return fail(c, DPM_EINVAL, "bad phantom id");
+  if (p->max_mat >= c->ht.n_mat) return fail(c, DPM_EINVAL, "phantom uses a material index beyond the tables");
+  if (src->particle != 0 && src->particle != 1) return fail(c, DPM_EINVAL, "particle must be 0 or 1");
+  if (src->spectrum != 0 && src->spectrum != 1) return fail(c, DPM_EINVAL, "spectrum must be 0 or 1");
+  const double emax = src->spectrum == 1 ? 6.0 : src->energy;
+  if (!(emax > 0) || emax > c->params.e_max) return fail(c, DPM_EINVAL, "source energy outside (0, e_max]");
+  if (!(src->sad > 0) || !(src->fx >= 0) || !(src->fy >= 0)) return fail(c, DPM_EINVAL, "bad beam geometry");
+  if (n > 0xFFFFFFFFull) return fail(c, DPM_EINVAL, "at most 2^32-1 histories per call");
+  if (n == 0) return DPM_OK;
+  dpm_run_opts o{};
+  if (opts) o = *opts;
+  int nb = o.n_batches > 0 ? o.n_batches : 50;
+  if (nb > 1024) return fail(c, DPM_EINVAL, "n_batches must be <= 1024");
+  if (uint64_t(nb) > n) nb = int(n);
+  const uint64_t bs = (n + nb - 1) / nb;
+  const int B = int((n + bs - 1) / bs);
+  cudaSetDevice(c->device);
+  int rc = update_mumax(c, p);
+  if (rc) return rc;
+  if (p->slab_batches < size_t(B)) {
+    cudaFree(p->d_slabs);
+    p->d_slabs = nullptr;
+    p->slab_batches = 0;
+    if ((rc = dalloc(c, &p->d_slabs, size_t(B) * p->V))) return rc;
+    p->slab_batches = size_t(B);
+  }
+  std::vector<double> inv_nb(B);
+  for (int b = 0; b < B; ++b) inv_nb[b] = 1.0 / double(std::min<uint64_t>(bs, n - uint64_t(b) * bs));
+  CUDA_TRY(c, cudaMemcpyAsync(p->d_inv_nb, inv_nb.data(), B * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(p->d_slabs, 0, size_t(B) * p->V * sizeof(unsigned long long), c->stream));
+
+  RunParams R{};
+  R.T = c->dt;
+  R.P.nx = p->nx; R.P.ny = p->ny; R.P.nz = p->nz;
+  R.P.dx = float(p->dx); R.P.dy = float(p->dy); R.P.dz = float(p->dz);
+  R.P.mat = p->d_mat;
+  R.P.rho = p->d_rho;
+  R.P.mu_max = p->d_mumax;
+  const double g = src->gantry_deg * 3.14159265358979323846 / 180.0;
+  const double ax[3] = {std::sin(g), 0.0, std::cos(g)};
+  R.S.particle = src->particle;
+  R.S.spectrum = src->spectrum;
+  R.S.energy = float(src->energy);
+  R.S.sx = float(src->iso[0] - src->sad * ax[0]);
+  R.S.sy = float(src->iso[1] - src->sad * ax[1]);
+  R.S.sz = float(src->iso[2] - src->sad * ax[2]);
+  R.S.cx = float(src->iso[0]);
+  R.S.cy = float(src->iso[1]);
+  R.S.cz = float(src->iso[2]);
+  R.S.e1x = float(std::cos(g));
+  R.S.e1z = float(-std::sin(g));
+  R.S.fx = float(src->fx);
+  R.S.fy = float(src->fy);
+  R.first = first;
+  R.n = n;
+  const uint64_t k = splitmix(seed);
+  R.key0 = uint32_t(k);
+  R.key1 = uint32_t(k >> 32);
+  R.n_batches = B;
+  R.slabs = p->d_slabs;
+  R.counters = p->d_counters;
+  R.err = c->d_err;
+
+  if (o.kernel == DPM_KERNEL_HISTORY) {
+    launch_history(R, bs, c->sm_count, o.block_size, c->stream);
+  } else {
+    std::string qerr;
+    int qrc = queue_run(c->queue, R, bs, o, c->sm_count, c->stream, qerr);
+    if (qrc) return fail(c, qrc, qerr);
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  launch_fold(p->d_slabs, B, p->V, p->d_inv_nb, p->d_S1, p->d_Q, c->sm_count, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  p->n_total += n;
+  p->b_total += uint64_t(B);
+  return DPM_OK;
+}
+
+int dpm_sync(dpm_ctx *c) {
+  if (!c) return DPM_EINVAL;
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  int e = 0;
+  CUDA_TRY(c, cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
+    if (e & ERR_OVERFLOW) return fail(c, DPM_EQUEUE_OVERFLOW, "particle stack or queue overflow");
+    if (e & ERR_TIMEOUT) return fail(c, DPM_ETIMEOUT, "a bounded device wait timed out");
+    return fail(c, DPM_ETIMEOUT, "a particle exceeded the step limit");
+  }
+  return DPM_OK;
+}
+
+static int read_common(dpm_ctx *c, PhantomState *p, double *d_dose, double *d_sigma, dpm_run_stats *st, int sync_rc) {
+  if (st) {
+    unsigned long long cnt[C_N];
+    CUDA_TRY(c, cudaMemcpy(cnt, p->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+    std::memset(st, 0, sizeof(*st));
+    st->n_histories = p->n_total;
+    st->n_batches = int32_t(p->b_total);
+    long long dep = 0;
+    std::vector<long long> s1(p->V);
+    CUDA_TRY(c, cudaMemcpy(s1.data(), p->d_S1, p->V * sizeof(long long), cudaMemcpyDeviceToHost));
+    for (long long x : s1) dep += x;
+    st->emitted = double((long long)cnt[C_EMIT]) / kTallyScale;
+    st->escaped = double((long long)cnt[C_ESC]) / kTallyScale;
+    st->missed = double((long long)cnt[C_MISS]) / kTallyScale;
+    st->deposited = double(dep) / kTallyScale;
+    st->n_e_steps = cnt[C_ESTEP];
+    st->n_g_flights = cnt[C_GFLIGHT];
+    st->n_g_interactions = cnt[C_GINT];
+    st->n_tally_atomics = cnt[C_ATOM];
+    st->n_pushed = cnt[C_PUSH];
+    st->error_flags = sync_rc == DPM_OK ? 0 : (sync_rc == DPM_EQUEUE_OVERFLOW ? 1 : 4);
+  }
+  (void)d_dose;
+  (void)d_sigma;
+  return DPM_OK;
+}
+
+int dpm_read_dose(dpm_ctx *c, int id, double *dose, double *sigma, int64_t *s1_raw, dpm_run_stats *st) {
+  if (!c) return DPM_EINVAL;
+  PhantomState *p = get_phantom(c, id);
+  if (!p) return fail(c, DPM_EINVAL, "bad phantom id");
+  const int src = dpm_sync(c);
+  if (src == DPM_ECUDA) return src;
+  std::string keep = c->err;
+  if (dose || sigma) {
+    int rc;
+    if (!p->d_dose && ((rc = dalloc(c, &p->d_dose, p->V)) || (rc = dalloc(c, &p->d_sigma, p->V)))) return rc;
+    launch_normalize(p->d_S1, p->d_Q, p->d_rho, p->V, double(p->n_total), double(p->b_total), p->dx * p->dy * p->dz,
+                     p->d_dose, p->d_sigma, c->sm_count, c->stream);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (dose) CUDA_TRY(c, cudaMemcpy(dose, p->d_dose, p->V * sizeof(double), cudaMemcpyDeviceToHost));
+    if (sigma) CUDA_TRY(c, cudaMemcpy(sigma, p->d_sigma, p->V * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  if (s1_raw) CUDA_TRY(c, cudaMemcpy(s1_raw, p->d_S1, p->V * sizeof(long long), cudaMemcpyDeviceToHost));
+  int rc = read_common(c, p, nullptr, nullptr, st, src);
+  if (rc) return rc;
+  if (src) c->err = keep;
+  return src;
+}
+
+int dpm_read_dose_device(dpm_ctx *c, int id, double *d_dose, double *d_sigma, dpm_run_stats *st) {
+  if (!c) return DPM_EINVAL;
+  PhantomState *p = get_phantom(c, id);
+  if (!p) return fail(c, DPM_EINVAL, "bad phantom id");
+  cudaSetDevice(c->device);
+  launch_normalize(p->d_S1, p->d_Q, p->d_rho, p->V, double(p->n_total), double(p->b_total), p->dx * p->dy * p->dz,
+                   d_dose, d_sigma, c->sm_count, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  if (!st) return DPM_OK;
+  const int src = dpm_sync(c);
+  if (src == DPM_ECUDA) return src;
+  std::string keep = c->err;
+  int rc = read_common(c, p, nullptr, nullptr, st, src);
+  if (rc) return rc;
+  if (src) c->err = keep;
+  return src;
+}
+
+// ---------------------------------------------------------------------------
+// diagnostics
+// ---------------------------------------------------------------------------
+int dpm_diag_table(dpm_ctx *c, int which, int mat, int n, const double *energy, const double *aux, double *out) {
+  if (!c) return DPM_EINVAL;
+  if (!c->tables_ready) return fail(c, DPM_ESTATE, "no tables");
+  if (n < 0 || (n > 0 && (!energy || !out)) || which < 0 || which > 9) return fail(c, DPM_EINVAL, "bad arguments");
+  if (which == 8 && n > 0 && !aux) return fail(c, DPM_EINVAL, "aux required");
+  DevPhantom P{};
+  if (which == 9) {
+    PhantomState *p = get_phantom(c, mat);
+    if (!p) return fail(c, DPM_EINVAL, "bad phantom id");
+    int rc = update_mumax(c, p);
+    if (rc) return rc;
+    P.mu_max = p->d_mumax;
+    mat = 0;
+  } else if (mat < 0 || mat >= c->ht.n_mat) {
+    return fail(c, DPM_EINVAL, "bad material");
+  }
+  if (n == 0) return DPM_OK;
+  cudaSetDevice(c->device);
+  double *d = nullptr;
+  int rc = dalloc(c, &d, size_t(3) * n);
+  if (rc) return rc;
+  cudaMemcpy(d, energy, n * sizeof(double), cudaMemcpyHostToDevice);
+  if (aux) cudaMemcpy(d + n, aux, n * sizeof(double), cudaMemcpyHostToDevice);
+  launch_diag_table(c->dt, P, which, mat, n, d, d + n, d + 2 * n, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(c, DPM_ECUDA, cudaGetErrorString(e));
+  return DPM_OK;
+}
+
+int dpm_diag_sample(dpm_ctx *c, int which, double e, double aux, int n, const double *u, double *out) {
+  if (!c) return DPM_EINVAL;
+  if (!c->tables_ready) return fail(c, DPM_ESTATE, "no tables");
+  if (n < 0 || (n > 0 && (!u || !out)) || which < 0 || which > 5) return fail(c, DPM_EINVAL, "bad arguments");
+  if (n == 0) return DPM_OK;
+  cudaSetDevice(c->device);
+  double *d = nullptr;
+  int rc = dalloc(c, &d, size_t(2) * n);
+  if (rc) return rc;
+  cudaMemcpy(d, u, n * sizeof(double), cudaMemcpyHostToDevice);
+  launch_diag_sample(c->dt, which, e, aux, n, d, d + n, c->stream);
+  cudaError_t er = cudaStreamSynchronize(c->stream);
+  if (er == cudaSuccess) er = cudaMemcpy(out, d + n, n * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (er != cudaSuccess) return fail(c, DPM_ECUDA, cudaGetErrorString(er));
+  return DPM_OK;
+}
+
+int dpm_diag_philox(dpm_ctx *c, int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
+  if (!c) return DPM_EINVAL;
+  if (n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(c, DPM_EINVAL, "bad arguments");
+  if (n == 0) return DPM_OK;
+  cudaSetDevice(c->device);
+  uint32_t *d = nullptr;
+  int rc = dalloc(c, &d, size_t(10) * n);
+  if (rc) return rc;
+  cudaMemcpy(d, ctr, 4 * n * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  cudaMemcpy(d + 4 * n, key, 2 * n * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  launch_diag_philox(n, d, d + 4 * n, d + 6 * n, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d + 6 * n, 4 * n * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(c, DPM_ECUDA, cudaGetErrorString(e));
+  return DPM_OK;
+}
+
+}  // extern "C"

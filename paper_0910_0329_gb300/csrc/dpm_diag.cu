@@ -1,0 +1,97 @@
+// dpm_diag.cu -- diagnostic kernels: evaluate the device tables and samplers
+// exactly as the transport kernels use them, so that the tests can compare
+// them element by element with the FP64 closed forms.
+#include <cuda_runtime.h>
+
+#include "dpm_device.cuh"
+#include "dpm_kernels.h"
+
+namespace dpm {
+
+__global__ void k_diag_table(DevTables T, DevPhantom P, int which, int mat, int n, const double *E, const double *aux,
+                             double *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float e = float(E[i]);
+  const EIdx x = eidx(T, e);
+  double r = 0.0;
+  switch (which) {
+    case 0: r = ph_at(T, mat, x).x; break;
+    case 1: r = ph_at(T, mat, x).y; break;
+    case 2: r = ph_at(T, mat, x).z; break;
+    case 3: r = el_at(T, mat, x).x; break;
+    case 4: r = el_at(T, mat, x).y; break;
+    case 5: r = el_at(T, mat, x).z; break;
+    case 6: r = el_at(T, mat, x).w; break;
+    case 7: r = lerp(T.pmol[size_t(mat) * T.n_e + x.i], T.pmol[size_t(mat) * T.n_e + x.i + 1], x.f); break;
+    case 8: {
+      const float4 a = el_at(T, mat, x);
+      r = csda_energy(T, mat, e, a.x, a.y, float(aux[i]));
+      break;
+    }
+    case 9: r = lerp(P.mu_max[x.i], P.mu_max[x.i + 1], x.f); break;
+    default: r = 0.0;
+  }
+  out[i] = r;
+}
+
+void launch_diag_table(const DevTables &T, const DevPhantom &P, int which, int mat, int n, const double *E,
+                       const double *aux, double *out, cudaStream_t st) {
+  k_diag_table<<<(n + 127) / 128, 128, 0, st>>>(T, P, which, mat, n, E, aux, out);
+}
+
+__global__ void k_diag_sample(DevTables T, int which, float e, float aux, int n, const double *u, double *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float x = float(u[i]);
+  const float lnE = logf(e);
+  const float k = e / kMc2f;
+  double r = 0.0;
+  switch (which) {
+    case 0: r = expf(samp(T.kn, lnE, x) * -log1pf(2.f * k)); break;
+    case 1: {
+      const float ec = T.wcc / e;
+      const float z = samp(T.mol, lnE, x);
+      r = 1.f / (1.f / ec - z * (1.f / ec - 2.f));
+      break;
+    }
+    case 2: r = fminf(T.wcr * expf(samp(T.brem, lnE, x) * logf(e / T.wcr)), e); break;
+    case 3: {
+      const float sq = sqrtf(fmaxf(1.f - 3.29744254f / k, 0.f));
+      const float lo = fmaxf(1.f / k, 0.5f * (1.f - sq)), hi = fminf(1.f - 1.f / k, 0.5f * (1.f + sq));
+      r = lo + samp(T.pair, lnE, x) * (hi - lo);
+      break;
+    }
+    case 4: {
+      // aux is the target mean q of 1 - mu: the kernel's argument is s/lambda1 = -ln(1-q)
+      const float A = msc_A(T, -log1pf(-aux));
+      r = msc_sample(A, x);
+      break;
+    }
+    case 5: r = spectrum_6mv(x); break;
+    default: r = 0.0;
+  }
+  out[i] = r;
+}
+
+void launch_diag_sample(const DevTables &T, int which, double e, double aux, int n, const double *u, double *out,
+                        cudaStream_t st) {
+  k_diag_sample<<<(n + 127) / 128, 128, 0, st>>>(T, which, float(e), float(aux), n, u, out);
+}
+
+__global__ void k_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+  const uint4 r = philox4x32_10(c, key[2 * i], key[2 * i + 1]);
+  out[4 * i] = r.x;
+  out[4 * i + 1] = r.y;
+  out[4 * i + 2] = r.z;
+  out[4 * i + 3] = r.w;
+}
+
+void launch_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, cudaStream_t st) {
+  k_diag_philox<<<(n + 127) / 128, 128, 0, st>>>(n, ctr, key, out);
+}
+
+}  // namespace dpm

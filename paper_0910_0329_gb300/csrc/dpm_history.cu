@@ -1,0 +1,180 @@
+// dpm_history.cu -- one-history-per-thread transport (the paper's own layout,
+// Sec. 2.2: each thread follows a source particle and all its secondaries
+// with a private stack), the batch fold and the dose normalisation.
+#include <cuda_runtime.h>
+
+#include "dpm_device.cuh"
+#include "dpm_kernels.h"
+
+namespace dpm {
+
+// Tally sink with run-length coalescing: consecutive deposits of one thread
+// into the same voxel are summed in a register and issued as one 64-bit
+// atomic add (exact, order-independent fixed point, 2^-32 MeV).
+struct HistSink {
+  const RunParams &R;
+  unsigned long long *slab = nullptr;
+  int pend_v = -1;
+  long long pend_q = 0;
+  long long cnt[C_N];
+  int err = 0;
+  Part *stack;
+  int sp = 0, cap;
+
+  __device__ HistSink(const RunParams &r, Part *st, int c) : R(r), stack(st), cap(c) {
+#pragma unroll
+    for (int i = 0; i < C_N; ++i) cnt[i] = 0;
+  }
+  __device__ __forceinline__ static long long fx(float e) { return __float2ll_rn(e * 4294967296.0f); }
+  __device__ __forceinline__ void flush() {
+    if (pend_v >= 0 && pend_q != 0) {
+      atomicAdd(slab + pend_v, (unsigned long long)pend_q);
+      ++cnt[C_ATOM];
+    }
+    pend_v = -1;
+    pend_q = 0;
+  }
+  __device__ __forceinline__ void deposit(int v, float dE) {
+    const long long q = fx(dE);
+    if (v == pend_v) {
+      pend_q += q;
+    } else {
+      flush();
+      pend_v = v;
+      pend_q = q;
+    }
+  }
+  __device__ __forceinline__ void escape(float E) { cnt[C_ESC] += fx(E); }
+  __device__ __forceinline__ void push(const Part &q) {
+    ++cnt[C_PUSH];
+    if (sp < cap) {
+      stack[sp++] = q;
+    } else {
+      err |= ERR_OVERFLOW;
+      cnt[C_ESC] += fx(q.E + (q.type == POSITRON ? 2.f * kMc2f : 0.f));
+    }
+  }
+  __device__ __forceinline__ void error(int e) { err |= e; }
+  __device__ __forceinline__ void count_step() { ++cnt[C_ESTEP]; }
+  __device__ __forceinline__ void count_flight() { ++cnt[C_GFLIGHT]; }
+  __device__ __forceinline__ void count_interaction() { ++cnt[C_GINT]; }
+};
+
+__device__ void reduce_counters(const long long *cnt, int err, const RunParams &R) {
+#pragma unroll
+  for (int i = 0; i < C_N; ++i) {
+    long long v = cnt[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd(R.counters + i, (unsigned long long)v);
+  }
+  int e = err;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e |= __shfl_down_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0 && e) atomicOr(R.err, e);
+}
+
+constexpr int kHistStack = 64;
+
+__global__ void __launch_bounds__(128) k_history(RunParams R, uint64_t batch_size) {
+  Part stack[kHistStack];
+  HistSink s(R, stack, kHistStack);
+  const size_t V = size_t(R.P.nx) * R.P.ny * R.P.nz;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t hl = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; hl < R.n; hl += stride) {
+    s.slab = R.slabs + (hl / batch_size) * V;
+    Part p;
+    const bool hit = make_primary(p, R, uint32_t(hl));
+    s.cnt[C_EMIT] += HistSink::fx(p.E);
+    if (!hit) {
+      s.cnt[C_MISS] += HistSink::fx(p.E);
+      continue;
+    }
+    s.sp = 0;
+    s.stack[s.sp++] = p;
+    while (s.sp > 0) {
+      Part q = s.stack[--s.sp];
+      if (q.type == PHOTON) {
+        int g = 0;
+        while (photon_segment(q, R, s)) {
+          if (++g >= kMaxPhotonSegments) {
+            s.error(ERR_STEPCAP);
+            s.deposit(vox(q, R.P), q.E);
+            break;
+          }
+        }
+      } else {
+        int n = 0;
+        while (electron_step(q, R, s)) {
+          if (++n >= kMaxElectronSteps) {
+            s.error(ERR_STEPCAP);
+            s.deposit(vox(q, R.P), q.E);
+            break;
+          }
+        }
+      }
+    }
+    s.flush();
+  }
+  reduce_counters(s.cnt, s.err, R);
+}
+
+void launch_history(const RunParams &R, uint64_t batch_size, int sm_count, int block, cudaStream_t st) {
+  if (block <= 0) block = 128;
+  block = 128;  // the kernel's launch bound
+  const uint64_t need = (R.n + block - 1) / block;
+  const uint64_t cap = uint64_t(sm_count) * 16;
+  const int grid = int(need < cap ? need : cap);
+  k_history<<<grid > 0 ? grid : 1, block, 0, st>>>(R, batch_size);
+}
+
+// Sum the batch slabs of one run into S1 (exact int64) and Q = sum_b d_b^2/n_b.
+__global__ void k_fold(const unsigned long long *slabs, int nb, size_t V, const double *inv_nb, long long *S1,
+                       double *Q) {
+  for (size_t v = size_t(blockIdx.x) * blockDim.x + threadIdx.x; v < V; v += size_t(gridDim.x) * blockDim.x) {
+    long long s = 0;
+    double q = 0.0;
+    for (int b = 0; b < nb; ++b) {
+      const long long d = (long long)slabs[size_t(b) * V + v];
+      s += d;
+      const double dd = double(d);
+      q += dd * dd * inv_nb[b];
+    }
+    S1[v] += s;
+    Q[v] += q;
+  }
+}
+
+void launch_fold(const unsigned long long *slabs, int nb, size_t V, const double *inv_nb, long long *S1, double *Q,
+                 int sm_count, cudaStream_t st) {
+  const size_t need = (V + 255) / 256;
+  const size_t cap = size_t(sm_count) * 8;
+  const int grid = int(need < cap ? need : cap);
+  k_fold<<<grid > 0 ? grid : 1, 256, 0, st>>>(slabs, nb, V, inv_nb, S1, Q);
+}
+
+// Dose (Gy per history) and its standard error from the batch statistics:
+// per-history variance (Q - S1^2/n)/(B - 1), sigma of the mean sqrt(var/n).
+__global__ void k_normalize(const long long *S1, const double *Q, const float *rho, size_t V, double n, double B,
+                            double vox_cm3, double *dose, double *sigma) {
+  for (size_t v = size_t(blockIdx.x) * blockDim.x + threadIdx.x; v < V; v += size_t(gridDim.x) * blockDim.x) {
+    const double s1 = double(S1[v]);
+    const double conv = kMeVtoJ / (double(rho[v]) * vox_cm3 * 1e-3) / kTallyScale;
+    if (dose) dose[v] = n > 0 ? s1 / n * conv : 0.0;
+    if (sigma) {
+      double var = 0.0;
+      if (B > 1.0 && n > 0) var = fmax(Q[v] - s1 * s1 / n, 0.0) / (B - 1.0);
+      sigma[v] = n > 0 ? sqrt(var / n) * conv : 0.0;
+    }
+  }
+}
+
+void launch_normalize(const long long *S1, const double *Q, const float *rho, size_t V, double n, double B,
+                      double vox_cm3, double *dose, double *sigma, int sm_count, cudaStream_t st) {
+  const size_t need = (V + 255) / 256;
+  const size_t cap = size_t(sm_count) * 8;
+  const int grid = int(need < cap ? need : cap);
+  k_normalize<<<grid > 0 ? grid : 1, 256, 0, st>>>(S1, Q, rho, V, n, B, vox_cm3, dose, sigma);
+}
+
+}  // namespace dpm

@@ -1,0 +1,98 @@
+// dpm_internal.h -- library-internal types shared by the host table builder,
+// the kernels and the C ABI.  Nothing here is part of the public interface.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <vector_types.h>
+
+#include "../../include/dpm.h"
+
+namespace dpm {
+
+constexpr double kMc2 = 0.51099895;        // electron rest energy, MeV (CODATA 2018)
+constexpr double kRe = 2.8179403262e-13;   // classical electron radius, cm
+constexpr double kAlpha = 7.2973525693e-3; // fine-structure constant
+constexpr double kNa = 6.02214076e23;      // Avogadro constant, 1/mol
+constexpr double kMeVtoJ = 1.602176634e-13;
+constexpr double kTallyScale = 4294967296.0; // 2^32 fixed-point quanta per MeV
+
+// One inverse-CDF sampling table: rows on a uniform ln(E) grid, columns on a
+// uniform grid in the uniform deviate u; entries are a normalised variable in
+// [0, 1] whose meaning depends on the process (see dpm_tables.cpp).
+struct SampTab {
+  const float *y;  // [ne][nu]
+  int ne, nu;
+  float lnE0, inv_dlnE;
+};
+
+// Device-side view of the tables.  Per-material arrays are [n_mat][n_e].
+struct DevTables {
+  int n_mat, n_e;
+  float lnE_lo, inv_dlnE;
+  const float4 *ph;    // {mu/rho total (cm^2/g), Compton fraction, photoelectric fraction, 0}
+  const float4 *el;    // {R (g/cm^2), S (MeV cm^2/g), Sigma_hard (cm^2/g), 1/lambda1 (cm^2/g)}
+  const float *pmol;   // Moller fraction of Sigma_hard
+  SampTab kn, mol, brem, pair;
+  const float *msc_lnA;  // ln A on a uniform grid of logit(q)
+  int msc_n;
+  float msc_x0, msc_inv_dx;
+  float eabs_e, eabs_g, wcc, wcr, f_e;
+};
+
+struct DevPhantom {
+  int nx, ny, nz;
+  float dx, dy, dz;
+  const uint8_t *mat;
+  const float *rho;
+  const float *mu_max;  // [n_e] photon majorant, 1/cm, on the tables' energy grid
+};
+
+struct DevSource {
+  int particle, spectrum;
+  float energy;
+  float sx, sy, sz;        // source point
+  float cx, cy, cz;        // isocentre
+  float e1x, e1z;          // field axis 1 (in the x-z plane); axis 2 is y
+  float fx, fy;
+};
+
+// Counters accumulated per thread and reduced at kernel exit.
+enum {
+  C_EMIT = 0, C_ESC, C_MISS,          // fixed-point energies (2^-32 MeV)
+  C_ESTEP, C_GFLIGHT, C_GINT, C_ATOM, C_PUSH,
+  C_N
+};
+
+enum { ERR_OVERFLOW = 1, ERR_STEPCAP = 2, ERR_TIMEOUT = 4 };
+
+struct RunParams {
+  DevTables T;
+  DevPhantom P;
+  DevSource S;
+  uint64_t first, n;       // history range
+  uint32_t key0, key1;     // Philox key from the seed
+  int n_batches;
+  unsigned long long *slabs;  // [n_batches][V]
+  unsigned long long *counters;  // [C_N] (energies as two's-complement int64)
+  int *err;
+};
+
+// Host-built tables (FP64 closed forms evaluated, stored as FP32).
+struct HostTables {
+  int n_mat = 0, n_e = 0;
+  double e_lo = 0, e_hi = 0;
+  std::vector<float> ph, el, pmol;
+  std::vector<float> kn, mol, brem, pair, msc;
+  int kn_ne = 0, mol_ne = 0, brem_ne = 0, pair_ne = 0, nu = 0, msc_n = 0;
+  double kn_lo = 0, kn_hi = 0, mol_lo = 0, mol_hi = 0, brem_lo = 0, brem_hi = 0, pair_lo = 0, pair_hi = 0;
+  double msc_x0 = 0, msc_x1 = 0;
+  std::vector<double> mu_mass_nodes;  // [n_mat][n_e] FP64 mu/rho for the majorant
+};
+
+bool build_tables(const dpm_material *mats, int n_mat, const dpm_table_params &p, HostTables &out,
+                  std::string &err);
+
+}  // namespace dpm

@@ -1,0 +1,22 @@
+// dpm_kernels.h -- host-side launchers of the library's kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dpm_internal.h"
+
+namespace dpm {
+
+void launch_history(const RunParams &R, uint64_t batch_size, int sm_count, int block, cudaStream_t st);
+void launch_fold(const unsigned long long *slabs, int nb, size_t V, const double *inv_nb, long long *S1, double *Q,
+                 int sm_count, cudaStream_t st);
+void launch_normalize(const long long *S1, const double *Q, const float *rho, size_t V, double n, double B,
+                      double vox_cm3, double *dose, double *sigma, int sm_count, cudaStream_t st);
+
+void launch_diag_table(const DevTables &T, const DevPhantom &P, int which, int mat, int n, const double *E,
+                       const double *aux, double *out, cudaStream_t st);
+void launch_diag_sample(const DevTables &T, int which, double e, double aux, int n, const double *u, double *out,
+                        cudaStream_t st);
+void launch_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, cudaStream_t st);
+
+}  // namespace dpm

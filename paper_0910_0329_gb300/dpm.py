@@ -1,0 +1,281 @@
+"""Thin ctypes binding of the C ABI in include/dpm.h (argument marshalling only).
+
+The module-level functions carry the ABI's names (``dpm_create``,
+``dpm_load_phantom``, ``dpm_build_tables``, ``dpm_run``, ``dpm_read_dose`` ...);
+``Dpm`` is a small convenience wrapper around them.  Every step of the
+transport runs in the CUDA library; if the library is missing or cannot load,
+this module raises -- there is no CPU fallback.  PyTorch is used only to pass a
+CUDA stream (``stream=torch.cuda.current_stream()``) or device output tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads as W
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libdpm.so")
+
+DPM_OK, DPM_EINVAL, DPM_ENOMEM, DPM_ECUDA, DPM_EQUEUE_OVERFLOW, DPM_ETIMEOUT, DPM_ESTATE = 0, -1, -2, -3, -4, -5, -6
+KERNEL_QUEUE, KERNEL_HISTORY = 0, 1
+_NAMES = {0: "DPM_OK", -1: "DPM_EINVAL", -2: "DPM_ENOMEM", -3: "DPM_ECUDA", -4: "DPM_EQUEUE_OVERFLOW",
+          -5: "DPM_ETIMEOUT", -6: "DPM_ESTATE"}
+
+
+class DpmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class dpm_material(C.Structure):
+    _fields_ = [("n_elem", C.c_int), ("Z", C.c_double * 8), ("A", C.c_double * 8), ("w", C.c_double * 8),
+                ("i_ev", C.c_double)]
+
+
+class dpm_table_params(C.Structure):
+    _fields_ = [("eabs_e", C.c_double), ("eabs_g", C.c_double), ("wcc", C.c_double), ("wcr", C.c_double),
+                ("f_e", C.c_double), ("c_pe", C.c_double), ("e_max", C.c_double), ("n_e", C.c_int)]
+
+
+class dpm_source(C.Structure):
+    _fields_ = [("particle", C.c_int), ("spectrum", C.c_int), ("energy", C.c_double), ("iso", C.c_double * 3),
+                ("sad", C.c_double), ("fx", C.c_double), ("fy", C.c_double), ("gantry_deg", C.c_double)]
+
+
+class dpm_run_opts(C.Structure):
+    _fields_ = [("kernel", C.c_int), ("n_batches", C.c_int), ("block_size", C.c_int), ("blocks_per_sm", C.c_int),
+                ("queue_log2", C.c_int), ("refill_min", C.c_int), ("timeout_s", C.c_double)]
+
+
+class dpm_run_stats(C.Structure):
+    _fields_ = [("n_histories", C.c_uint64), ("n_batches", C.c_int32), ("error_flags", C.c_int32),
+                ("emitted", C.c_double), ("deposited", C.c_double), ("escaped", C.c_double), ("missed", C.c_double),
+                ("n_e_steps", C.c_uint64), ("n_g_flights", C.c_uint64), ("n_g_interactions", C.c_uint64),
+                ("n_tally_atomics", C.c_uint64), ("n_pushed", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# Every symbol declared in include/dpm.h with its ctypes signature.
+_P = C.c_void_p
+_SIGS = {
+    "dpm_create": (C.c_int, [C.POINTER(_P), C.c_int]),
+    "dpm_destroy": (None, [_P]),
+    "dpm_last_error": (C.c_char_p, [_P]),
+    "dpm_set_stream": (C.c_int, [_P, _P]),
+    "dpm_load_phantom": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, _P, _P,
+                                   C.POINTER(C.c_int)]),
+    "dpm_free_phantom": (C.c_int, [_P, C.c_int]),
+    "dpm_build_tables": (C.c_int, [_P, C.POINTER(dpm_material), C.c_int, C.POINTER(dpm_table_params)]),
+    "dpm_run": (C.c_int, [_P, C.c_int, C.POINTER(dpm_source), C.c_uint64, C.c_uint64, C.c_uint64,
+                          C.POINTER(dpm_run_opts)]),
+    "dpm_reset_tally": (C.c_int, [_P, C.c_int]),
+    "dpm_read_dose": (C.c_int, [_P, C.c_int, _P, _P, _P, C.POINTER(dpm_run_stats)]),
+    "dpm_read_dose_device": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(dpm_run_stats)]),
+    "dpm_sync": (C.c_int, [_P]),
+    "dpm_diag_table": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
+    "dpm_diag_sample": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, _P, _P]),
+    "dpm_diag_philox": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"CUDA library missing at {_LIB_PATH}; build it with __graft_entry__.build()")
+        L = C.CDLL(_LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(ctx, rc):
+    if rc != DPM_OK:
+        msg = lib().dpm_last_error(ctx).decode() if ctx else ""
+        raise DpmError(rc, msg)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_P)
+
+
+# ---------------------------------------------------------------------------
+# ABI-named wrappers
+# ---------------------------------------------------------------------------
+def dpm_create(device: int = 0):
+    h = _P()
+    rc = lib().dpm_create(C.byref(h), device)
+    _check(None, rc)
+    return h
+
+
+def dpm_destroy(ctx):
+    lib().dpm_destroy(ctx)
+
+
+def dpm_set_stream(ctx, stream=None):
+    """``stream``: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(ctx, lib().dpm_set_stream(ctx, _P(raw) if raw else None))
+
+
+def dpm_load_phantom(ctx, ph: W.Phantom) -> int:
+    mat = np.ascontiguousarray(ph.mat, np.uint8)
+    rho = np.ascontiguousarray(ph.rho, np.float32)
+    if mat.size != ph.n_vox or rho.size != ph.n_vox:
+        raise ValueError("phantom arrays do not match its shape")
+    pid = C.c_int(-1)
+    _check(ctx, lib().dpm_load_phantom(ctx, ph.nx, ph.ny, ph.nz, ph.dx, ph.dy, ph.dz, _ptr(mat), _ptr(rho),
+                                       C.byref(pid)))
+    return pid.value
+
+
+def dpm_free_phantom(ctx, pid: int):
+    _check(ctx, lib().dpm_free_phantom(ctx, pid))
+
+
+def material_struct(md: dict) -> dpm_material:
+    m = dpm_material()
+    m.n_elem = len(md["elements"])
+    for k, (Z, A, w) in enumerate(md["elements"]):
+        m.Z[k], m.A[k], m.w[k] = Z, A, w
+    m.i_ev = md["i_ev"]
+    return m
+
+
+def params_struct(p: dict) -> dpm_table_params:
+    return dpm_table_params(p["eabs_e"], p["eabs_g"], p["wcc"], p["wcr"], p["f_e"], p["c_pe"], p["e_max"],
+                            int(p["n_e"]))
+
+
+def dpm_build_tables(ctx, materials, params: dict):
+    arr = (dpm_material * len(materials))(*[material_struct(m) for m in materials])
+    pp = params_struct(params)
+    _check(ctx, lib().dpm_build_tables(ctx, arr, len(materials), C.byref(pp)))
+
+
+def source_struct(src: W.Source) -> dpm_source:
+    s = dpm_source()
+    s.particle, s.spectrum, s.energy = src.particle, src.spectrum, src.energy
+    for k in range(3):
+        s.iso[k] = src.iso[k]
+    s.sad, s.fx, s.fy, s.gantry_deg = src.sad, src.fx, src.fy, src.gantry_deg
+    return s
+
+
+def dpm_run(ctx, pid: int, src: W.Source, first: int, n: int, seed: int, opts: dpm_run_opts | None = None):
+    s = source_struct(src)
+    _check(ctx, lib().dpm_run(ctx, pid, C.byref(s), first, n, seed, C.byref(opts) if opts is not None else None))
+
+
+def dpm_reset_tally(ctx, pid: int):
+    _check(ctx, lib().dpm_reset_tally(ctx, pid))
+
+
+def dpm_read_dose(ctx, pid: int, n_vox: int, want_dose=True, want_sigma=True, want_raw=True):
+    dose = np.zeros(n_vox, np.float64) if want_dose else None
+    sigma = np.zeros(n_vox, np.float64) if want_sigma else None
+    raw = np.zeros(n_vox, np.int64) if want_raw else None
+    st = dpm_run_stats()
+    rc = lib().dpm_read_dose(ctx, pid, _ptr(dose) if dose is not None else None,
+                             _ptr(sigma) if sigma is not None else None, _ptr(raw) if raw is not None else None,
+                             C.byref(st))
+    _check(ctx, rc)
+    return dose, sigma, raw, st.as_dict()
+
+
+def dpm_read_dose_device(ctx, pid: int, dose_t, sigma_t):
+    """Write dose and sigma into caller-allocated CUDA float64 tensors."""
+    st = dpm_run_stats()
+    _check(ctx, lib().dpm_read_dose_device(ctx, pid, _P(dose_t.data_ptr()), _P(sigma_t.data_ptr()), C.byref(st)))
+    return st.as_dict()
+
+
+def dpm_sync(ctx):
+    _check(ctx, lib().dpm_sync(ctx))
+
+
+def dpm_diag_table(ctx, which: int, mat: int, energy, aux=None) -> np.ndarray:
+    e = np.ascontiguousarray(energy, np.float64)
+    a = np.ascontiguousarray(aux, np.float64) if aux is not None else None
+    out = np.zeros(e.size, np.float64)
+    _check(ctx, lib().dpm_diag_table(ctx, which, mat, e.size, _ptr(e), _ptr(a) if a is not None else None, _ptr(out)))
+    return out
+
+
+def dpm_diag_sample(ctx, which: int, e: float, aux: float, u) -> np.ndarray:
+    uu = np.ascontiguousarray(u, np.float64)
+    out = np.zeros(uu.size, np.float64)
+    _check(ctx, lib().dpm_diag_sample(ctx, which, e, aux, uu.size, _ptr(uu), _ptr(out)))
+    return out
+
+
+def dpm_diag_philox(ctx, ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, np.uint32).reshape(-1)
+    k = np.ascontiguousarray(key, np.uint32).reshape(-1)
+    n = c.size // 4
+    if k.size != 2 * n:
+        raise ValueError("need 4 counter words and 2 key words per block")
+    out = np.zeros(4 * n, np.uint32)
+    _check(ctx, lib().dpm_diag_philox(ctx, n, _ptr(c), _ptr(k), _ptr(out)))
+    return out.reshape(n, 4)
+
+
+def run_opts(kernel=KERNEL_QUEUE, n_batches=0, block_size=0, blocks_per_sm=0, queue_log2=0, refill_min=0,
+             timeout_s=0.0) -> dpm_run_opts:
+    return dpm_run_opts(kernel, n_batches, block_size, blocks_per_sm, queue_log2, refill_min, timeout_s)
+
+
+class Dpm:
+    """Convenience wrapper: one context, tables built from a parameter dict."""
+
+    def __init__(self, device=0, materials=None, params=None, stream=None):
+        self.ctx = dpm_create(device)
+        if stream is not None:
+            dpm_set_stream(self.ctx, stream)
+        self.phantoms = {}
+        if materials is not None:
+            self.build_tables(materials, params or W.DEFAULT_PARAMS)
+
+    def build_tables(self, materials, params):
+        dpm_build_tables(self.ctx, materials, params)
+
+    def load_phantom(self, ph: W.Phantom) -> int:
+        pid = dpm_load_phantom(self.ctx, ph)
+        self.phantoms[pid] = ph
+        return pid
+
+    def run(self, pid, src, n, seed, first=0, **opts):
+        dpm_run(self.ctx, pid, src, first, n, seed, run_opts(**opts) if opts else None)
+
+    def read(self, pid):
+        return dpm_read_dose(self.ctx, pid, self.phantoms[pid].n_vox)
+
+    def reset(self, pid):
+        dpm_reset_tally(self.ctx, pid)
+
+    def close(self):
+        if self.ctx:
+            dpm_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

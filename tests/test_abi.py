@@ -1,0 +1,50 @@
+"""CPU checks of the boundary: the C-ABI library builds for sm_103a, loads,
+and exports every symbol that include/dpm.h declares; the Python binding
+covers exactly those symbols.  No CUDA call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_0910_0329_gb300 import build_lib, dpm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "dpm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dpm_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary_calls():
+    names = declared_symbols()
+    for required in ["dpm_load_phantom", "dpm_build_tables", "dpm_run", "dpm_read_dose"]:
+        assert required in names
+
+
+def test_library_builds_loads_and_exports_every_declared_symbol():
+    path = build_lib.build()
+    L = ctypes.CDLL(path)
+    missing = [n for n in declared_symbols() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_exactly_the_declared_symbols():
+    assert sorted(dpm._SIGS) == declared_symbols()
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(dpm, "_LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(dpm, "_lib", None)
+    with pytest.raises(ImportError):
+        dpm.lib()
+
+
+def test_struct_layouts_match_header():
+    # sizes of the ABI structs as laid out by the C compiler (x86-64 / aarch64 LP64)
+    assert ctypes.sizeof(dpm.dpm_material) == 4 + 4 + 3 * 8 * 8 + 8
+    assert ctypes.sizeof(dpm.dpm_table_params) == 7 * 8 + 8
+    assert ctypes.sizeof(dpm.dpm_source) == 8 + 8 + 3 * 8 + 4 * 8
+    assert ctypes.sizeof(dpm.dpm_run_opts) == 6 * 4 + 8

@@ -1,0 +1,125 @@
+"""Dose parity of the CUDA path against the FP64 oracle (statistical, since the
+two draw from different generators): in voxels with D > 10 % D_max at least
+95 % agree within 2 combined standard deviations, and the energy deposited
+per history agrees within 0.2 %.  The oracle runs with history-by-history
+variance; the GPU with the batch method.  History counts are chosen so that
+the combined standard error of the integral is well below 0.2 %."""
+import dataclasses
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_0910_0329_gb300 import dpm
+from paper_0910_0329_gb300 import workloads as W
+
+from parity_util import compare
+
+pytestmark = pytest.mark.gpu
+KERNELS = [dpm.KERNEL_HISTORY, dpm.KERNEL_QUEUE]
+WORKERS = os.cpu_count() or 1
+
+# name -> (workload factory, oracle histories, GPU histories)
+CASES = {
+    "e20_wlw_61x61x60": (W.c0_electron_wlw, 20000, 400000),
+    "6mv_wbw_61x61x60": (W.c1_photon_wbw, 3_000_000, 20_000_000),
+    "e20_blob128": (W.c2_electron_blob128, 16000, 400000),
+}
+
+_oracle_cache = {}
+
+
+def oracle_result(name):
+    if name not in _oracle_cache:
+        make, n_o, _ = CASES[name]
+        wl = make()
+        _oracle_cache[name] = (wl, O.run(wl.phantom, W.MATERIALS, wl.params, wl.source, n_o, 1000 + wl.seed,
+                                         workers=WORKERS))
+    return _oracle_cache[name]
+
+
+def gpu_run(wl, n, kernel, seed=None, params=None, n_batches=50, first=0):
+    with dpm.Dpm(0, W.MATERIALS, params or wl.params) as d:
+        pid = d.load_phantom(wl.phantom)
+        d.run(pid, wl.source, n, wl.seed if seed is None else seed, first=first, kernel=kernel, n_batches=n_batches)
+        return d.read(pid)
+
+
+@pytest.mark.parametrize("kernel", KERNELS, ids=["history", "queue"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_dose_parity(name, kernel):
+    wl, orc = oracle_result(name)
+    n_g = CASES[name][2]
+    dose, sigma, raw, st = gpu_run(wl, n_g, kernel)
+    assert st["error_flags"] == 0
+    r = compare(wl.phantom, dose, sigma, raw, n_g, orc)
+    print(name, kernel, r)
+    assert r["n_vox"] > 500
+    assert r["pass_frac"] >= 0.95, r
+    assert abs(r["z_mean"]) < 0.15 and 0.8 < r["z_std"] < 1.2, r
+    assert r["e_rel_sigma"] < 0.2e-2 / 2.5, r  # the 0.2 % test must be meaningful
+    assert abs(r["e_rel_diff"]) < 0.2e-2, r
+    bal = abs(st["emitted"] - st["deposited"] - st["escaped"] - st["missed"]) / st["emitted"]
+    assert bal < 1e-5
+
+
+@pytest.mark.parametrize("kernel", KERNELS, ids=["history", "queue"])
+def test_pairs_and_positrons(kernel):
+    """15 MeV photon pencil in water: pair production and annihilation."""
+    ph = W.slab_phantom(21, 21, 40, 0.5, [(0, 1e9, W.MAT_WATER, 1.0)])
+    X, Y, _ = ph.extent
+    src = W.Source(W.PHOTON, W.SPEC_MONO, 15.0, (X / 2, Y / 2, 0.0), 100.0, 0.2, 0.2)
+    wl = W.Workload("pair", ph, src, 0, 31)
+    params = dict(W.DEFAULT_PARAMS, e_max=16.0)
+    wl.params = params
+    orc = O.run(ph, W.MATERIALS, params, src, 300000, 77, workers=WORKERS)
+    assert orc.stats["n_positrons"] > 1000
+    dose, sigma, raw, st = gpu_run(wl, 3_000_000, kernel)
+    r = compare(ph, dose, sigma, raw, 3_000_000, orc)
+    print(r)
+    assert r["pass_frac"] >= 0.95 and abs(r["e_rel_diff"]) < max(0.2e-2, 3 * r["e_rel_sigma"]), r
+
+
+@pytest.mark.parametrize("kernel", KERNELS, ids=["history", "queue"])
+def test_single_voxel_phantom(kernel):
+    ph = W.slab_phantom(1, 1, 1, 2.0, [(0, 1e9, W.MAT_WATER, 1.0)])
+    src = W.Source(W.PHOTON, W.SPEC_MONO, 1.0, (1.0, 1.0, 0.0), 100.0, 1.0, 1.0)
+    wl = W.Workload("one", ph, src, 0, 5)
+    orc = O.run(ph, W.MATERIALS, wl.params, src, 400000, 5, workers=WORKERS)
+    dose, sigma, raw, st = gpu_run(wl, 4_000_000, kernel)
+    d_o = orc.S1[0] / orc.n
+    s_o = orc.sigma_mean_energy()[0]
+    d_g = raw[0] / 2.0 ** 32 / 4_000_000
+    assert abs(d_g - d_o) < 3 * np.hypot(s_o, s_o * np.sqrt(orc.n / 4e6))
+
+
+@pytest.mark.parametrize("kernel", KERNELS, ids=["history", "queue"])
+def test_ragged_small_phantom_and_batches(kernel):
+    """4x5x3 voxels of unequal size, 1001 histories in 50 batches (unequal)."""
+    ph = W.Phantom(4, 5, 3, 0.7, 0.4, 1.1, np.array([0, 2, 1] * 20, np.uint8),
+                   np.array([1.0, 1.85, 0.3] * 20, np.float32))
+    src = W.Source(W.ELECTRON, W.SPEC_MONO, 3.0, (1.4, 1.0, 0.0), 100.0, 1.0, 1.0)
+    wl = W.Workload("ragged", ph, src, 0, 9)
+    dose, sigma, raw, st = gpu_run(wl, 1001, kernel)
+    assert st["n_histories"] == 1001 and st["n_batches"] == 48  # ceil(1001 / ceil(1001/50))
+    assert np.isfinite(dose).all() and np.isfinite(sigma).all() and (sigma >= 0).all()
+    orc = O.run(ph, W.MATERIALS, wl.params, src, 20000, 3, workers=WORKERS)
+    dose2, sigma2, raw2, st2 = gpu_run(wl, 200000, kernel)
+    r = compare(ph, dose2, sigma2, raw2, 200000, orc)
+    assert r["pass_frac"] >= 0.9 and abs(r["e_rel_diff"]) < max(0.2e-2, 3 * r["e_rel_sigma"]), r
+
+
+@pytest.mark.parametrize("kernel", KERNELS, ids=["history", "queue"])
+def test_missed_beam_and_empty_run(kernel):
+    wl = W.c1_photon_wbw()
+    src = dataclasses.replace(wl.source, iso=(-50.0, -50.0, 10.0))
+    with dpm.Dpm(0, W.MATERIALS, wl.params) as d:
+        pid = d.load_phantom(wl.phantom)
+        d.run(pid, src, 0, 1, kernel=kernel)
+        _, _, raw0, st0 = d.read(pid)
+        assert raw0.sum() == 0 and st0["n_histories"] == 0
+        d.run(pid, src, 5000, 1, kernel=kernel)
+        dose, sigma, raw, st = d.read(pid)
+    assert raw.sum() == 0 and dose.sum() == 0
+    assert st["missed"] == pytest.approx(st["emitted"], rel=1e-9)
