@@ -1,0 +1,317 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the coupled electron-photon Monte Carlo transport.
+
+One step = one dpm_run of the whole hot path (source sampling, photon Woodcock
+tracking and interactions, condensed-history electron steps, hard events,
+fixed-point tally, batch fold) over 10^7 histories of the synthetic 6 MV beam
+on the 61x61x60 water/bone/water phantom, with inputs resident on the device.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank transports its own history range on its own
+GPU (no data-path collective; weak scaling) and rank 0 prints one JSON line.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead
+(rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--kernel", choices=["queue", "history"], default="history")
+    ap.add_argument("--workload", default="6mv_wbw_61x61x60")
+    ap.add_argument("--histories", type=int, default=0, help="histories per step (default: the workload's)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU work of the oracle baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def run_reference(args, rank):
+    """The FP64 oracle on the host cores (the reference arm)."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_0910_0329_gb300 import workloads as W
+
+    wl = W.WORKLOADS[args.workload](n_histories=1)
+    cores = os.cpu_count() or 1
+    # calibrate: per-history cost on one core
+    t = time.perf_counter()
+    O.run(wl.phantom, W.MATERIALS, wl.params, wl.source, 2000, 99, workers=1)
+    per_hist = (time.perf_counter() - t) / 2000
+    n_step = max(cores * 64, int(cores * 3.0 / per_hist))  # about 3 s of wall time per step
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        O.run(wl.phantom, W.MATERIALS, wl.params, wl.source, n_step, 1000 + i, workers=cores)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t)
+    ms = 1000 * statistics.mean(times)
+    value = n_step / (ms / 1000)
+    line = {"impl": "reference", "metric": "histories/s", "value": value, "unit": "histories/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "histories_per_step": n_step,
+                       "program": "FP64 single-thread-per-process oracle (oracle/dpm_oracle.c), RANECU"},
+            "cpu_baseline": {"value": value, "unit": "histories/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n_step} histories of {args.workload} per step"},
+            "e2e": {"value": value, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(args, wl):
+    from oracle import oracle as O
+    from paper_0910_0329_gb300 import workloads as W
+
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    O.run(wl.phantom, W.MATERIALS, wl.params, wl.source, 1000, 99, workers=1)
+    per_hist = (time.perf_counter() - t) / 1000
+    n = max(cores * 64, int(args.cpu_seconds / per_hist))
+    t = time.perf_counter()
+    O.run(wl.phantom, W.MATERIALS, wl.params, wl.source, n, 7, workers=cores)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "histories/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} histories of {args.workload} (about {args.cpu_seconds:.0f} s of CPU work), "
+                      f"{cores} worker processes"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as tdist
+
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        tdist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank)
+        if world > 1:
+            import torch.distributed as tdist
+
+            tdist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_0910_0329_gb300 import build_lib, dpm
+    from paper_0910_0329_gb300 import workloads as W
+
+    build_lib.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    wl = W.WORKLOADS[args.workload]()
+    n = args.histories or wl.n_histories
+    kernel = dpm.KERNEL_QUEUE if args.kernel == "queue" else dpm.KERNEL_HISTORY
+    ph = wl.phantom
+    d = dpm.Dpm(local, W.MATERIALS, wl.params, stream=stream)
+    pid = d.load_phantom(ph)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
+
+    def step(i):
+        d.run(pid, wl.source, n, wl.seed, first=(rank + world * i) * n, kernel=kernel)
+
+    # warm-up
+    for i in range(args.warmup):
+        step(1000 + i)
+    d.read(pid)
+    d.reset(pid)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        import torch.distributed as tdist
+
+        tdist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    t_wall = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)  # write 256 MiB (> L2) between steps, outside the step events
+            ev[i][0].record(stream)
+            step(i)
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as tdist
+
+        t = torch.tensor([tot_ms], device=f"cuda:{local}")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        tdist.barrier()
+    dose, sigma, raw, st = d.read(pid)
+    n_tot = n * args.steps
+    value = world * n_tot / (tot_ms / 1000.0)
+
+    # statistical efficiency: sigma at D_max after n_tot histories -> time to 1 %
+    imax = int(np.argmax(dose))
+    rel = float(sigma[imax] / dose[imax]) if dose[imax] > 0 else float("nan")
+    n_1pct = n_tot * (rel / 0.01) ** 2
+    t_1pct = n_1pct / value
+    hi = dose > 0.5 * dose.max()
+    mean_rel_50 = float(np.mean(sigma[hi] / dose[hi]))
+
+    # roofline of the transport kernel: algorithmic bytes per history are the
+    # 8-byte tally atomics, the 44-byte records each secondary is pushed and
+    # popped as, and the primary's record
+    peak, peak_kind = measured_peaks()
+    t_kernel_s = st["transport_ms"] / 1000.0 / max(st["n_transport_launches"], 1)
+    hist_per_launch = n
+    atom_per_hist = st["n_tally_atomics"] / n_tot
+    sec_per_hist = st["n_pushed"] / n_tot
+    bytes_per_hist = 8 * atom_per_hist + 88 * sec_per_hist + 44
+    achieved = bytes_per_hist * hist_per_launch / t_kernel_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_kind": peak_kind, "kernel": "k_queue" if kernel == dpm.KERNEL_QUEUE else "k_history",
+            "kernel_ms_per_launch": t_kernel_s * 1000, "bytes_per_history": bytes_per_hist,
+            "tally_atomics_per_history": atom_per_hist, "secondaries_per_history": sec_per_hist,
+            "kernel_share_of_step": st["transport_ms"] / max(tot_ms, 1e-9)}
+
+    launches_per_step = 3 if kernel == dpm.KERNEL_QUEUE else 2  # (queue init +) transport + fold
+
+    line = {"metric": "histories/s", "value": value, "unit": "histories/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "histories_per_step": n, "phantom": f"{ph.nx}x{ph.ny}x{ph.nz}",
+                       "kernel": args.kernel, "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"{world} replica(s), disjoint history ranges"},
+            "time_to_1pct_sigma_at_dmax_s": t_1pct, "sigma_rel_at_dmax": rel, "histories_accumulated": n_tot * world,
+            "mean_sigma_rel_above_half_dmax": mean_rel_50,
+            "roofline": roof, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
+            "wall_s_timed_region": wall,
+            "energy_balance_rel": abs(st["emitted"] - st["deposited"] - st["escaped"] - st["missed"]) / st["emitted"]}
+
+    if not args.no_e2e:
+        line["e2e"] = e2e(args, d, wl, n, kernel, local)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, wl)
+    d.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as tdist
+
+        tdist.destroy_process_group()
+
+
+def e2e(args, d, wl, n, kernel, local):
+    """Same metric through the public C ABI with host buffers: every step
+    copies the phantom from pinned host memory, transports, and reads dose and
+    sigma back into host memory."""
+    import torch
+
+    from paper_0910_0329_gb300 import dpm
+
+    ph = wl.phantom
+    mat = torch.from_numpy(ph.mat).pin_memory()
+    rho = torch.from_numpy(ph.rho).pin_memory()
+    dose = torch.empty(ph.n_vox, dtype=torch.float64).pin_memory()
+    sig = torch.empty(ph.n_vox, dtype=torch.float64).pin_memory()
+    s1 = torch.empty(ph.n_vox, dtype=torch.int64).pin_memory()
+    L = dpm.lib()
+    times = []
+    steps = max(3, min(args.steps, 5))
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        pid = dpm.dpm_load_phantom_raw(d.ctx, ph.nx, ph.ny, ph.nz, ph.dx, ph.dy, ph.dz, mat.data_ptr(), rho.data_ptr())
+        dpm.dpm_run(d.ctx, pid, wl.source, i * n, n, wl.seed, dpm.run_opts(kernel=kernel))
+        st = dpm.dpm_run_stats()
+        rc = L.dpm_read_dose(d.ctx, pid, dose.data_ptr(), sig.data_ptr(), s1.data_ptr(), dpm.C.byref(st))
+        if rc:
+            raise dpm.DpmError(rc, L.dpm_last_error(d.ctx).decode())
+        dpm.dpm_free_phantom(d.ctx, pid)
+        if i > 0:
+            times.append(time.perf_counter() - t)
+    t = statistics.mean(times)
+    return {"value": n / t, "unit": "histories/s", "h2d_bytes_per_step": ph.n_vox * 5,
+            "d2h_bytes_per_step": ph.n_vox * (8 + 8 + 8) + 8 * 8 + 4,
+            "what": "dpm_load_phantom (pinned host mat+rho) + dpm_run + dpm_read_dose (host dose, sigma, raw)"}
+
+
+if __name__ == "__main__":
+    main()

@@ -95,7 +95,10 @@ typedef struct {
     int queue_log2;    /* log2 of each particle queue's capacity */
     int refill_min;    /* lanes that must be idle before a warp refills */
     double timeout_s;  /* bound on any device wait (default 20 s) */
+    int physics_flags; /* DPM_NO_HARD: no Moller/bremsstrahlung events; DPM_NO_MSC: no
+                          elastic deflections (test and ablation switches; 0 = full physics) */
 } dpm_run_opts;
+enum { DPM_NO_HARD = 1, DPM_NO_MSC = 2 };
 
 /* Run summary returned by dpm_read_dose(). Energies in MeV. */
 typedef struct {
@@ -106,6 +109,10 @@ typedef struct {
     uint64_t n_e_steps, n_g_flights, n_g_interactions;
     uint64_t n_tally_atomics;     /* 64-bit atomic adds issued to the tally */
     uint64_t n_pushed;            /* secondaries created */
+    double transport_ms;          /* device time of the transport kernels of the runs read
+                                     (CUDA events recorded around each launch on its stream) */
+    double fold_ms;               /* device time of the batch folds of those runs */
+    uint64_t n_transport_launches;/* transport kernel launches since the previous read */
 } dpm_run_stats;
 
 int dpm_create(dpm_ctx **out, int cuda_device);
@@ -124,7 +131,9 @@ int dpm_free_phantom(dpm_ctx *ctx, int phantom_id);
 
 /* Build the FP32 device tables (per-material attenuation, range, stopping
    power, hard cross sections, transport mean free path; inverse-CDF sampling
-   tables) from FP64 closed forms of the model.  Must precede dpm_run(). */
+   tables) from FP64 closed forms of the model.  The per-material tables have
+   n_e nodes uniformly spaced in ln E from 0.99*min(eabs_e, eabs_g) to
+   1.01*e_max and are interpolated linearly.  Must precede dpm_run(). */
 int dpm_build_tables(dpm_ctx *ctx, const dpm_material *mats, int n_mat, const dpm_table_params *p);
 
 /* Transport histories [first_history, first_history + n_histories) from

@@ -41,7 +41,14 @@ struct PhantomState {
   double *d_dose = nullptr, *d_sigma = nullptr;
   uint64_t n_total = 0;
   uint64_t b_total = 0;
+  // CUDA events around each transport launch and fold since the last read
+  std::vector<cudaEvent_t> ev;
 };
+
+void drop_events(PhantomState *p) {
+  for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+  p->ev.clear();
+}
 
 }  // namespace
 
@@ -89,6 +96,7 @@ int dalloc(dpm_ctx *c, T **p, size_t n) {
 
 void free_phantom(PhantomState *p) {
   if (!p) return;
+  drop_events(p);
   cudaFree(p->d_mat);
   cudaFree(p->d_rho);
   cudaFree(p->d_mumax);
@@ -303,6 +311,8 @@ int dpm_reset_tally(dpm_ctx *c, int id) {
   CUDA_TRY(c, cudaMemsetAsync(p->d_counters, 0, C_N * sizeof(unsigned long long), c->stream));
   p->n_total = 0;
   p->b_total = 0;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  drop_events(p);
   return DPM_OK;
 }
 
@@ -343,8 +353,10 @@ int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t 
   CUDA_TRY(c, cudaMemcpyAsync(p->d_inv_nb, inv_nb.data(), B * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(p->d_slabs, 0, size_t(B) * p->V * sizeof(unsigned long long), c->stream));
 
+  if (o.physics_flags & ~(DPM_NO_HARD | DPM_NO_MSC)) return fail(c, DPM_EINVAL, "unknown physics flag");
   RunParams R{};
   R.T = c->dt;
+  R.T.flags = o.physics_flags;
   R.P.nx = p->nx; R.P.ny = p->ny; R.P.nz = p->nz;
   R.P.dx = float(p->dx); R.P.dy = float(p->dy); R.P.dz = float(p->dz);
   R.P.mat = p->d_mat;
@@ -375,16 +387,22 @@ int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t 
   R.counters = p->d_counters;
   R.err = c->d_err;
 
+  cudaEvent_t ev[3];
+  for (int i = 0; i < 3; ++i) CUDA_TRY(c, cudaEventCreate(&ev[i]));
+  for (int i = 0; i < 3; ++i) p->ev.push_back(ev[i]);
   if (o.kernel == DPM_KERNEL_HISTORY) {
+    CUDA_TRY(c, cudaEventRecord(ev[0], c->stream));
     launch_history(R, bs, c->sm_count, o.block_size, c->stream);
   } else {
     std::string qerr;
-    int qrc = queue_run(c->queue, R, bs, o, c->sm_count, c->stream, qerr);
+    int qrc = queue_run(c->queue, R, bs, o, c->sm_count, c->stream, ev[0], qerr);
     if (qrc) return fail(c, qrc, qerr);
   }
   CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaEventRecord(ev[1], c->stream));
   launch_fold(p->d_slabs, B, p->V, p->d_inv_nb, p->d_S1, p->d_Q, c->sm_count, c->stream);
   CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaEventRecord(ev[2], c->stream));
   p->n_total += n;
   p->b_total += uint64_t(B);
   return DPM_OK;
@@ -405,7 +423,8 @@ int dpm_sync(dpm_ctx *c) {
   return DPM_OK;
 }
 
-static int read_common(dpm_ctx *c, PhantomState *p, double *d_dose, double *d_sigma, dpm_run_stats *st, int sync_rc) {
+// Fill the run summary; s1_host (if not NULL) already holds the integer tally.
+static int read_common(dpm_ctx *c, PhantomState *p, const int64_t *s1_host, dpm_run_stats *st, int sync_rc) {
   if (st) {
     unsigned long long cnt[C_N];
     CUDA_TRY(c, cudaMemcpy(cnt, p->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost));
@@ -413,9 +432,13 @@ static int read_common(dpm_ctx *c, PhantomState *p, double *d_dose, double *d_si
     st->n_histories = p->n_total;
     st->n_batches = int32_t(p->b_total);
     long long dep = 0;
-    std::vector<long long> s1(p->V);
-    CUDA_TRY(c, cudaMemcpy(s1.data(), p->d_S1, p->V * sizeof(long long), cudaMemcpyDeviceToHost));
-    for (long long x : s1) dep += x;
+    if (s1_host) {
+      for (size_t v = 0; v < p->V; ++v) dep += s1_host[v];
+    } else {
+      std::vector<long long> s1(p->V);
+      CUDA_TRY(c, cudaMemcpy(s1.data(), p->d_S1, p->V * sizeof(long long), cudaMemcpyDeviceToHost));
+      for (long long x : s1) dep += x;
+    }
     st->emitted = double((long long)cnt[C_EMIT]) / kTallyScale;
     st->escaped = double((long long)cnt[C_ESC]) / kTallyScale;
     st->missed = double((long long)cnt[C_MISS]) / kTallyScale;
@@ -425,10 +448,16 @@ static int read_common(dpm_ctx *c, PhantomState *p, double *d_dose, double *d_si
     st->n_g_interactions = cnt[C_GINT];
     st->n_tally_atomics = cnt[C_ATOM];
     st->n_pushed = cnt[C_PUSH];
+    for (size_t i = 0; i + 2 < p->ev.size(); i += 3) {
+      float a = 0, b = 0;
+      if (cudaEventElapsedTime(&a, p->ev[i], p->ev[i + 1]) == cudaSuccess) st->transport_ms += a;
+      if (cudaEventElapsedTime(&b, p->ev[i + 1], p->ev[i + 2]) == cudaSuccess) st->fold_ms += b;
+      st->n_transport_launches++;
+    }
+    cudaGetLastError();
+    drop_events(p);
     st->error_flags = sync_rc == DPM_OK ? 0 : (sync_rc == DPM_EQUEUE_OVERFLOW ? 1 : 4);
   }
-  (void)d_dose;
-  (void)d_sigma;
   return DPM_OK;
 }
 
@@ -450,7 +479,7 @@ int dpm_read_dose(dpm_ctx *c, int id, double *dose, double *sigma, int64_t *s1_r
     if (sigma) CUDA_TRY(c, cudaMemcpy(sigma, p->d_sigma, p->V * sizeof(double), cudaMemcpyDeviceToHost));
   }
   if (s1_raw) CUDA_TRY(c, cudaMemcpy(s1_raw, p->d_S1, p->V * sizeof(long long), cudaMemcpyDeviceToHost));
-  int rc = read_common(c, p, nullptr, nullptr, st, src);
+  int rc = read_common(c, p, s1_raw, st, src);
   if (rc) return rc;
   if (src) c->err = keep;
   return src;
@@ -468,7 +497,7 @@ int dpm_read_dose_device(dpm_ctx *c, int id, double *d_dose, double *d_sigma, dp
   const int src = dpm_sync(c);
   if (src == DPM_ECUDA) return src;
   std::string keep = c->err;
-  int rc = read_common(c, p, nullptr, nullptr, st, src);
+  int rc = read_common(c, p, nullptr, st, src);
   if (rc) return rc;
   if (src) c->err = keep;
   return src;

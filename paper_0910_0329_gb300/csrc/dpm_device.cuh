@@ -503,7 +503,7 @@ __device__ bool electron_step(Part &p, const RunParams &R, Sink &s) {
   const float Rend = el_at(T, m, eidx(T, Tend)).x;
   const float sE = fmaxf(r0.x - Rend, 0.f) / rho;
   const uint4 rn = draw(p, R);
-  const float sh = r0.z > 0.f ? -logf(u01(rn.x)) / (rho * r0.z) : kInf;
+  const float sh = (r0.z > 0.f && !(T.flags & DPM_NO_HARD)) ? -logf(u01(rn.x)) / (rho * r0.z) : kInf;
   const bool hard = sh < sE;
   const float st = hard ? sh : sE;
   const float tau = u01(rn.y);
@@ -518,9 +518,11 @@ __device__ bool electron_step(Part &p, const RunParams &R, Sink &s) {
   } else {
     const float th = tau * st;
     move(p, th);
-    const float A = msc_A(T, rho * st * r0.w);
-    const float omc = msc_sample(A, u01(rn.z));
-    rotate(p.u, p.v, p.w, 1.f - omc, kTwoPi * u01(rn.w));
+    if (!(T.flags & DPM_NO_MSC)) {
+      const float A = msc_A(T, rho * st * r0.w);
+      const float omc = msc_sample(A, u01(rn.z));
+      rotate(p.u, p.v, p.w, 1.f - omc, kTwoPi * u01(rn.w));
+    }
     const float rest = st - th;
     const float t2 = dist_to_face(p, P, axis);
     if (t2 <= rest) {

@@ -8,7 +8,7 @@
 
 #include <vector_types.h>
 
-#include "../../include/dpm.h"
+#include "dpm.h"
 
 namespace dpm {
 
@@ -40,6 +40,7 @@ struct DevTables {
   int msc_n;
   float msc_x0, msc_inv_dx;
   float eabs_e, eabs_g, wcc, wcr, f_e;
+  int flags;  // DPM_NO_HARD / DPM_NO_MSC
 };
 
 struct DevPhantom {

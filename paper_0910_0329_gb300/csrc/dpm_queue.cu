@@ -1,13 +1,524 @@
-// dpm_queue.cu -- persistent transport kernel with particle queues.
+// dpm_queue.cu -- persistent transport kernel with device-wide particle queues.
+//
+// The paper runs one history per thread, so the 32 threads of a warp follow
+// statistically independent paths and execute mostly one at a time (its
+// Sec. 4 diagnosis of the C1060 speed-up).  Here every warp holds particles of
+// ONE type (photons or electrons/positrons) in its lanes, steps them together,
+// and refills lanes that have finished from per-type particle queues;
+// secondaries are pushed to those queues with one atomic per warp.  The
+// physics of a particle is the same code as in the per-history kernel and its
+// random numbers are keyed by its identity, so both kernels produce the same
+// integer tally.
+//
+// Queues: for each type, one ring per CTA ("shard") in global memory, SoA, with
+// a sequence number per slot (a producer publishes position p by writing p+1,
+// the consumer frees the slot for position p+capacity), so that producers and
+// consumers on different SMs never read a half-written record.  A warp pushes
+// to its CTA's shard and pops from it first, stealing from other shards when it
+// is empty.  The run ends when every started warp is idle, every queue is empty
+// and the source is exhausted.  Every wait is bounded by a time limit read from
+// %globaltimer; on expiry the kernel records an error and returns.
+#include <cuda_runtime.h>
+
+#include "dpm_device.cuh"
 #include "dpm_queue.h"
 
 namespace dpm {
 
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kQBlock = 128;
+constexpr int kStealProbes = 8;
+
+struct alignas(128) Ctl {
+  unsigned long long v;
+  unsigned long long pad[15];
+};
+
+struct QType {
+  float *x, *y, *z, *u, *v, *w, *E;
+  uint32_t *vox, *idl, *idh, *hist, *seq;
+  Ctl *head, *tail;  // [K]
+};
+
+struct QDev {
+  QType q[2];  // 0 photons, 1 electrons and positrons
+  int K, log2cs;
+  uint32_t mask;
+  Ctl *next_hist, *idle, *started;
+  int refill_min;
+  uint32_t high_water;
+  unsigned long long timeout_ns;   // bound on any single wait
+  unsigned long long deadline_ns;  // bound on the whole launch (from kernel start)
+  uint64_t batch_size;
+};
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long *p) {
+  return *(const volatile unsigned long long *)p;
+}
+
+__device__ __forceinline__ uint32_t ld_volatile32(const uint32_t *p) { return *(const volatile uint32_t *)p; }
+
+// Occupancy of a shard from two relaxed loads.  The loads of head and tail
+// may be observed in either order, so a concurrent consumer can make head
+// appear ahead of tail: the difference saturates at zero.
+__device__ __forceinline__ unsigned long long occupancy(unsigned long long head, unsigned long long tail) {
+  return tail > head ? tail - head : 0ull;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Lane-level sink: tally with run-length coalescing, counters, and queue pushes.
+struct QSink {
+  const RunParams &R;
+  const QDev &Q;
+  int home;
+  unsigned long long *slab = nullptr;
+  int pend_v = -1;
+  long long pend_q = 0;
+  long long cnt[C_N];
+  int err = 0;
+
+  __device__ QSink(const RunParams &r, const QDev &q, int h) : R(r), Q(q), home(h) {
+#pragma unroll
+    for (int i = 0; i < C_N; ++i) cnt[i] = 0;
+  }
+  __device__ __forceinline__ static long long fx(float e) { return __float2ll_rn(e * 4294967296.0f); }
+  __device__ __forceinline__ void flush() {
+    if (pend_v >= 0 && pend_q != 0) {
+      atomicAdd(slab + pend_v, (unsigned long long)pend_q);
+      ++cnt[C_ATOM];
+    }
+    pend_v = -1;
+    pend_q = 0;
+  }
+  __device__ __forceinline__ void deposit(int v, float dE) {
+    const long long q = fx(dE);
+    if (v == pend_v) {
+      pend_q += q;
+    } else {
+      flush();
+      pend_v = v;
+      pend_q = q;
+    }
+  }
+  __device__ __forceinline__ void escape(float E) { cnt[C_ESC] += fx(E); }
+  __device__ __forceinline__ void error(int e) { err |= e; }
+  __device__ __forceinline__ void count_step() { ++cnt[C_ESTEP]; }
+  __device__ __forceinline__ void count_flight() { ++cnt[C_GFLIGHT]; }
+  __device__ __forceinline__ void count_interaction() { ++cnt[C_GINT]; }
+
+  // Warp-aggregated push of the lanes that are here together: one atomic on
+  // the shard's tail per queue type, then each lane writes its record and
+  // publishes its slot.
+  __device__ void push(const Part &q) {
+    ++cnt[C_PUSH];
+    const int t = (q.type == PHOTON) ? 0 : 1;
+    const unsigned act = __activemask();
+    const unsigned mt = __ballot_sync(act, t == 1);
+    // one round per queue type; the masks are the same in every active lane
+    for (int tt = 0; tt < 2; ++tt) {
+      const unsigned mask = tt ? mt : (act & ~mt);
+      if (mask == 0 || t != tt) continue;
+      push_one(q, tt, mask);
+    }
+  }
+
+  __device__ void push_one(const Part &q, int t, unsigned mask) {
+    const int leader = __ffs(mask) - 1;
+    const int rank = __popc(mask & lanemask_lt());
+    const QType &Qt = Q.q[t];
+    unsigned long long base = 0;
+    int room = 1;
+    if ((int)(threadIdx.x & 31) == leader) {
+      const unsigned long long h = ld_volatile(&Qt.head[home].v);
+      const unsigned long long tl = ld_volatile(&Qt.tail[home].v);
+      const unsigned long long cap = 1ull << Q.log2cs;
+      if (occupancy(h, tl) + __popc(mask) > cap - 64) room = 0;
+      else base = atomicAdd(&Qt.tail[home].v, (unsigned long long)__popc(mask));
+    }
+    base = __shfl_sync(mask, base, leader);
+    room = __shfl_sync(mask, room, leader);
+    if (!room) {
+      err |= ERR_OVERFLOW;
+      cnt[C_ESC] += fx(q.E + (q.type == POSITRON ? 2.f * kMc2f : 0.f));
+      return;
+    }
+    const unsigned long long p = base + rank;
+    const uint32_t slot = uint32_t(p) & Q.mask;
+    const size_t idx = (size_t(home) << Q.log2cs) + slot;
+    // wait for the consumer of position p - capacity to have freed the slot
+    if (ld_volatile32(Qt.seq + idx) != uint32_t(p)) {
+      const unsigned long long t0 = now_ns();
+      while (ld_volatile32(Qt.seq + idx) != uint32_t(p)) {
+        if (now_ns() - t0 > Q.timeout_ns) {
+          err |= ERR_TIMEOUT;
+          return;
+        }
+        __nanosleep(64);
+      }
+    }
+    Qt.x[idx] = q.x;
+    Qt.y[idx] = q.y;
+    Qt.z[idx] = q.z;
+    Qt.u[idx] = q.u;
+    Qt.v[idx] = q.v;
+    Qt.w[idx] = q.w;
+    Qt.E[idx] = q.E;
+    Qt.vox[idx] = uint32_t(q.ix) | (uint32_t(q.iy) << 11) | (uint32_t(q.iz) << 22);
+    Qt.idl[idx] = q.id_lo;
+    Qt.idh[idx] = q.id_hi;
+    Qt.hist[idx] = q.hist | (q.type == POSITRON ? 0x80000000u : 0u);
+    __threadfence();
+    *(volatile uint32_t *)(Qt.seq + idx) = uint32_t(p + 1);
+  }
+};
+
+// Leader claims up to `want` queued positions of shard s with a CAS on its
+// head; returns the count (warp-uniform) and the first position.
+__device__ __forceinline__ int claim(const QType &Qt, int s, int want, unsigned long long &base) {
+  int n = 0;
+  unsigned long long b = 0;
+  if ((threadIdx.x & 31) == 0) {
+    for (int tries = 0; tries < 32; ++tries) {
+      const unsigned long long h = ld_volatile(&Qt.head[s].v);
+      const unsigned long long t = ld_volatile(&Qt.tail[s].v);
+      if (t <= h) break;
+      const unsigned long long k = min(t - h, (unsigned long long)want);
+      if (atomicCAS(&Qt.head[s].v, h, h + k) == h) {
+        n = int(k);
+        b = h;
+        break;
+      }
+    }
+  }
+  n = __shfl_sync(kFull, n, 0);
+  base = __shfl_sync(kFull, b, 0);
+  return n;
+}
+
+// Read the record at position p of shard s (waiting for its publication) and
+// free the slot for the producer one lap later.
+__device__ __forceinline__ bool take(const QDev &Q, int t, int s, unsigned long long p, Part &o, int &err) {
+  const QType &Qt = Q.q[t];
+  const uint32_t slot = uint32_t(p) & Q.mask;
+  const size_t idx = (size_t(s) << Q.log2cs) + slot;
+  if (ld_volatile32(Qt.seq + idx) != uint32_t(p + 1)) {
+    const unsigned long long t0 = now_ns();
+    while (ld_volatile32(Qt.seq + idx) != uint32_t(p + 1)) {
+      if (now_ns() - t0 > Q.timeout_ns) {
+        err |= ERR_TIMEOUT;
+        return false;
+      }
+      __nanosleep(32);
+    }
+  }
+  __threadfence();
+  o.x = __ldcg(Qt.x + idx);
+  o.y = __ldcg(Qt.y + idx);
+  o.z = __ldcg(Qt.z + idx);
+  o.u = __ldcg(Qt.u + idx);
+  o.v = __ldcg(Qt.v + idx);
+  o.w = __ldcg(Qt.w + idx);
+  o.E = __ldcg(Qt.E + idx);
+  const uint32_t vx = __ldcg(Qt.vox + idx);
+  o.ix = int(vx & 0x7ffu);
+  o.iy = int((vx >> 11) & 0x7ffu);
+  o.iz = int(vx >> 22);
+  o.id_lo = __ldcg(Qt.idl + idx);
+  o.id_hi = __ldcg(Qt.idh + idx);
+  const uint32_t h = __ldcg(Qt.hist + idx);
+  o.hist = h & 0x7fffffffu;
+  o.type = t == 0 ? PHOTON : ((h >> 31) ? POSITRON : ELECTRON);
+  o.ctr = 0;
+  __threadfence();
+  *(volatile uint32_t *)(Qt.seq + idx) = uint32_t(p + (1ull << Q.log2cs));
+  return true;
+}
+
+// Fill the warp's empty lanes from queue t (home shard first, then a few
+// others).  Returns the number of lanes filled (warp-uniform).
+__device__ int refill_queue(const QDev &Q, int t, int home, int probes, unsigned empty, Part &p, bool &alive,
+                            int &err) {
+  const int want = __popc(empty);
+  if (want == 0) return 0;
+  const int lane = threadIdx.x & 31;
+  unsigned long long base;
+  int s = home;
+  int n = claim(Q.q[t], s, want, base);
+  for (int k = 1; n == 0 && k <= probes && k < Q.K; ++k) {
+    s = (home + k * 97) % Q.K;
+    n = claim(Q.q[t], s, want, base);
+  }
+  if (n == 0) return 0;
+  if (empty & (1u << lane)) {
+    const int rank = __popc(empty & lanemask_lt());
+    if (rank < n) alive = take(Q, t, s, base + rank, p, err);
+  }
+  return n;
+}
+
+// Start new source histories in the empty lanes.
+__device__ int refill_source(const RunParams &R, const QDev &Q, unsigned empty, Part &p, bool &alive, QSink &sk) {
+  const int want = __popc(empty);
+  if (want == 0) return 0;
+  const int lane = threadIdx.x & 31;
+  unsigned long long b = 0;
+  if (lane == 0) b = atomicAdd(&Q.next_hist->v, (unsigned long long)want);
+  b = __shfl_sync(kFull, b, 0);
+  if (b >= R.n) return 0;
+  if (empty & (1u << lane)) {
+    const unsigned long long hl = b + __popc(empty & lanemask_lt());
+    if (hl < R.n) {
+      const bool hit = make_primary(p, R, uint32_t(hl));
+      sk.cnt[C_EMIT] += QSink::fx(p.E);
+      if (!hit) sk.cnt[C_MISS] += QSink::fx(p.E);
+      alive = hit;
+    }
+  }
+  return int(min((unsigned long long)want, R.n - b));
+}
+
+// Any queued particle anywhere, or histories left to start (warp-uniform).
+__device__ bool any_work(const RunParams &R, const QDev &Q) {
+  bool w = false;
+  for (int s = threadIdx.x & 31; s < Q.K && !w; s += 32)
+    for (int t = 0; t < 2; ++t)
+      if (occupancy(ld_volatile(&Q.q[t].head[s].v), ld_volatile(&Q.q[t].tail[s].v)) > 0) w = true;
+  if ((threadIdx.x & 31) == 0 && ld_volatile(&Q.next_hist->v) < R.n) w = true;
+  return __any_sync(kFull, w);
+}
+
+__device__ bool source_allowed(const RunParams &R, const QDev &Q, int home) {
+  bool ok = true;
+  if ((threadIdx.x & 31) == 0) {
+    for (int t = 0; t < 2; ++t)
+      if (occupancy(ld_volatile(&Q.q[t].head[home].v), ld_volatile(&Q.q[t].tail[home].v)) > Q.high_water) ok = false;
+    if (ld_volatile(&Q.next_hist->v) >= R.n) ok = false;
+  }
+  return __shfl_sync(kFull, ok, 0);
+}
+
+__device__ void reduce_counters_q(const long long *cnt, int err, const RunParams &R) {
+#pragma unroll
+  for (int i = 0; i < C_N; ++i) {
+    long long v = cnt[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd(R.counters + i, (unsigned long long)v);
+  }
+  int e = err;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e |= __shfl_down_sync(kFull, e, o);
+  if ((threadIdx.x & 31) == 0 && e) atomicOr(R.err, e);
+}
+
+__global__ void __launch_bounds__(kQBlock) k_queue(RunParams R, QDev Q) {
+  const int lane = threadIdx.x & 31;
+  const int home = blockIdx.x % Q.K;
+  const int src_type = (R.S.particle == 0) ? 0 : 1;
+  const size_t V = size_t(R.P.nx) * R.P.ny * R.P.nz;
+  if (lane == 0) atomicAdd(&Q.started->v, 1ull);
+  QSink sk(R, Q, home);
+  Part p{};
+  bool alive = false;
+  int nstep = 0;
+  int mode = -1;  // warp-uniform: type of the particles in the lanes, -1 when empty
+  bool idle = false;
+  unsigned long long idle_t0 = 0;
+  unsigned sleep_ns = 128;
+  const unsigned long long t_start = __shfl_sync(kFull, now_ns(), 0);
+  for (;;) {
+    unsigned live = __ballot_sync(kFull, alive);
+    if (live == 0) mode = -1;
+    if (32 - __popc(live) >= Q.refill_min || live == 0) {
+      const unsigned empty = ~live;
+      const bool was_alive = alive;
+      if (mode < 0) {
+        // electrons first (they carry most of the work), then photons, then
+        // new histories; other shards are searched only when all that fails
+        if (refill_queue(Q, 1, home, 0, empty, p, alive, sk.err)) mode = 1;
+        else if (refill_queue(Q, 0, home, 0, empty, p, alive, sk.err)) mode = 0;
+        else if (source_allowed(R, Q, home) && refill_source(R, Q, empty, p, alive, sk)) mode = src_type;
+        else if (refill_queue(Q, 1, home, kStealProbes, empty, p, alive, sk.err)) mode = 1;
+        else if (refill_queue(Q, 0, home, kStealProbes, empty, p, alive, sk.err)) mode = 0;
+      } else if (mode == src_type) {
+        if (!refill_queue(Q, mode, home, 0, empty, p, alive, sk.err) && source_allowed(R, Q, home))
+          refill_source(R, Q, empty, p, alive, sk);
+      } else {
+        refill_queue(Q, mode, home, kStealProbes, empty, p, alive, sk.err);
+      }
+      if (alive && !was_alive) {
+        sk.slab = R.slabs + (uint64_t(p.hist) / Q.batch_size) * V;
+        nstep = 0;
+      }
+      live = __ballot_sync(kFull, alive);
+    }
+    if (live == 0) {
+      // nothing in the lanes: idle until work appears or the run is over
+      if (!idle) {
+        __threadfence();
+        if (lane == 0) atomicAdd(&Q.idle->v, 1ull);
+        idle = true;
+        idle_t0 = now_ns();
+      }
+      if (any_work(R, Q)) {
+        if (lane == 0) atomicAdd(&Q.idle->v, ~0ull);  // -1
+        idle = false;
+        sleep_ns = 128;
+        if (__shfl_sync(kFull, now_ns() - t_start > Q.deadline_ns, 0)) {
+          sk.error(ERR_TIMEOUT);
+          break;
+        }
+        continue;
+      }
+      bool done = false;
+      if (lane == 0) done = ld_volatile(&Q.idle->v) == ld_volatile(&Q.started->v);
+      done = __shfl_sync(kFull, done, 0);
+      if (done) {
+        __threadfence();
+        if (!any_work(R, Q)) break;
+      }
+      const bool expired = __shfl_sync(kFull, now_ns() - idle_t0 > Q.timeout_ns, 0);
+      if (expired) {
+        sk.error(ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(sleep_ns);
+      sleep_ns = min(sleep_ns * 2, 16384u);
+      continue;
+    }
+    if (alive) {
+      if (mode == 0) {
+        alive = photon_segment(p, R, sk);
+        if (alive && ++nstep >= kMaxPhotonSegments) {
+          sk.error(ERR_STEPCAP);
+          sk.deposit(vox(p, R.P), p.E);
+          alive = false;
+        }
+      } else {
+        alive = electron_step(p, R, sk);
+        if (alive && ++nstep >= kMaxElectronSteps) {
+          sk.error(ERR_STEPCAP);
+          sk.deposit(vox(p, R.P), p.E);
+          alive = false;
+        }
+      }
+      if (!alive) sk.flush();
+    }
+  }
+  sk.flush();
+  reduce_counters_q(sk.cnt, sk.err, R);
+}
+
+__global__ void k_queue_init(uint32_t *seq0, uint32_t *seq1, size_t n, uint32_t mask) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    seq0[i] = uint32_t(i) & mask;
+    seq1[i] = uint32_t(i) & mask;
+  }
+}
+
+}  // namespace
+
 int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_run_opts &o, int sm_count,
-              cudaStream_t st, std::string &err) {
-  (void)q; (void)R; (void)batch_size; (void)o; (void)sm_count; (void)st;
-  err = "queue kernel not built yet";
-  return DPM_EINVAL;
+              cudaStream_t st, cudaEvent_t start, std::string &err) {
+  if (R.n > 0x7fffffffull) {
+    err = "the queue kernel takes at most 2^31-1 histories per call";
+    return DPM_EINVAL;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_queue, kQBlock, 0);
+  if (e != cudaSuccess || per_sm < 1) {
+    err = std::string("occupancy query failed: ") + cudaGetErrorString(e);
+    return DPM_ECUDA;
+  }
+  if (o.block_size != 0 && o.block_size != kQBlock) {
+    // the block shape is fixed by the kernel's launch bound; more warps per SM
+    // come from more blocks
+  }
+  int bps = o.blocks_per_sm > 0 ? std::min(o.blocks_per_sm, per_sm) : per_sm;
+  const int K = sm_count * bps;
+  const int log2cs = o.queue_log2 > 0 ? o.queue_log2 : 13;
+  if (log2cs < 7 || log2cs > 20) {
+    err = "queue_log2 must be in [7, 20]";
+    return DPM_EINVAL;
+  }
+  const size_t cs = size_t(1) << log2cs;
+  const size_t slots = size_t(K) * cs;
+  const size_t per_type = slots * 12 * sizeof(uint32_t) + 2 * size_t(K) * sizeof(Ctl);
+  const size_t bytes = 2 * per_type + 3 * sizeof(Ctl) + 256;
+  if (q.bytes < bytes) {
+    if (q.mem) cudaFree(q.mem);
+    q.mem = nullptr;
+    q.bytes = 0;
+    e = cudaMalloc(&q.mem, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      err = std::string("queue allocation: ") + cudaGetErrorString(e);
+      return DPM_ENOMEM;
+    }
+    q.bytes = bytes;
+  }
+  q.log2_cap = log2cs;
+  QDev Q{};
+  char *m = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(q.mem) + 127) & ~uintptr_t(127));
+  Q.next_hist = reinterpret_cast<Ctl *>(m);
+  Q.idle = Q.next_hist + 1;
+  Q.started = Q.next_hist + 2;
+  char *ctl_end = m + 3 * sizeof(Ctl);
+  for (int t = 0; t < 2; ++t) {
+    QType &T = Q.q[t];
+    char *b = ctl_end + t * per_type;
+    T.head = reinterpret_cast<Ctl *>(b);
+    T.tail = T.head + K;
+    uint32_t *f = reinterpret_cast<uint32_t *>(b + 2 * size_t(K) * sizeof(Ctl));
+    float **fl[7] = {&T.x, &T.y, &T.z, &T.u, &T.v, &T.w, &T.E};
+    for (int i = 0; i < 7; ++i) *fl[i] = reinterpret_cast<float *>(f + i * slots);
+    T.vox = f + 7 * slots;
+    T.idl = f + 8 * slots;
+    T.idh = f + 9 * slots;
+    T.hist = f + 10 * slots;
+    T.seq = f + 11 * slots;
+  }
+  Q.K = K;
+  Q.log2cs = log2cs;
+  Q.mask = uint32_t(cs - 1);
+  Q.refill_min = o.refill_min > 0 ? std::min(o.refill_min, 32) : 8;
+  Q.high_water = uint32_t(cs / 4);
+  const double tmo = o.timeout_s > 0 ? o.timeout_s : 20.0;
+  Q.timeout_ns = (unsigned long long)(tmo * 1e9);
+  // the whole launch: the wait bound plus 2 us per history (a hundred times the
+  // cost of a 20 MeV electron history on this path)
+  Q.deadline_ns = Q.timeout_ns + (unsigned long long)(double(R.n) * 2000.0);
+  Q.batch_size = batch_size;
+  // zero the control words of both types and the three run counters
+  e = cudaMemsetAsync(m, 0, 3 * sizeof(Ctl), st);
+  for (int t = 0; t < 2 && e == cudaSuccess; ++t)
+    e = cudaMemsetAsync(Q.q[t].head, 0, 2 * size_t(K) * sizeof(Ctl), st);
+  if (e != cudaSuccess) {
+    err = cudaGetErrorString(e);
+    return DPM_ECUDA;
+  }
+  k_queue_init<<<sm_count * 4, 256, 0, st>>>(Q.q[0].seq, Q.q[1].seq, slots, Q.mask);
+  cudaEventRecord(start, st);
+  k_queue<<<K, kQBlock, 0, st>>>(R, Q);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err = cudaGetErrorString(e);
+    return DPM_ECUDA;
+  }
+  return DPM_OK;
 }
 
 void queue_free(QueueState &q) {

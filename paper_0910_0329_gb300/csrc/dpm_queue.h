@@ -16,8 +16,9 @@ struct QueueState {
 };
 
 // Launch the persistent kernel for one run; returns a dpm_status code.
+// `start` is recorded on the stream just before the transport kernel.
 int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_run_opts &o, int sm_count,
-              cudaStream_t st, std::string &err);
+              cudaStream_t st, cudaEvent_t start, std::string &err);
 void queue_free(QueueState &q);
 
 }  // namespace dpm

@@ -20,6 +20,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "
 
 DPM_OK, DPM_EINVAL, DPM_ENOMEM, DPM_ECUDA, DPM_EQUEUE_OVERFLOW, DPM_ETIMEOUT, DPM_ESTATE = 0, -1, -2, -3, -4, -5, -6
 KERNEL_QUEUE, KERNEL_HISTORY = 0, 1
+NO_HARD, NO_MSC = 1, 2
 _NAMES = {0: "DPM_OK", -1: "DPM_EINVAL", -2: "DPM_ENOMEM", -3: "DPM_ECUDA", -4: "DPM_EQUEUE_OVERFLOW",
           -5: "DPM_ETIMEOUT", -6: "DPM_ESTATE"}
 
@@ -47,14 +48,16 @@ class dpm_source(C.Structure):
 
 class dpm_run_opts(C.Structure):
     _fields_ = [("kernel", C.c_int), ("n_batches", C.c_int), ("block_size", C.c_int), ("blocks_per_sm", C.c_int),
-                ("queue_log2", C.c_int), ("refill_min", C.c_int), ("timeout_s", C.c_double)]
+                ("queue_log2", C.c_int), ("refill_min", C.c_int), ("timeout_s", C.c_double),
+                ("physics_flags", C.c_int)]
 
 
 class dpm_run_stats(C.Structure):
     _fields_ = [("n_histories", C.c_uint64), ("n_batches", C.c_int32), ("error_flags", C.c_int32),
                 ("emitted", C.c_double), ("deposited", C.c_double), ("escaped", C.c_double), ("missed", C.c_double),
                 ("n_e_steps", C.c_uint64), ("n_g_flights", C.c_uint64), ("n_g_interactions", C.c_uint64),
-                ("n_tally_atomics", C.c_uint64), ("n_pushed", C.c_uint64)]
+                ("n_tally_atomics", C.c_uint64), ("n_pushed", C.c_uint64), ("transport_ms", C.c_double),
+                ("fold_ms", C.c_double), ("n_transport_launches", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -237,8 +240,9 @@ def dpm_diag_philox(ctx, ctr, key) -> np.ndarray:
 
 
 def run_opts(kernel=KERNEL_QUEUE, n_batches=0, block_size=0, blocks_per_sm=0, queue_log2=0, refill_min=0,
-             timeout_s=0.0) -> dpm_run_opts:
-    return dpm_run_opts(kernel, n_batches, block_size, blocks_per_sm, queue_log2, refill_min, timeout_s)
+             timeout_s=0.0, physics_flags=0) -> dpm_run_opts:
+    return dpm_run_opts(kernel, n_batches, block_size, blocks_per_sm, queue_log2, refill_min, timeout_s,
+                        physics_flags)
 
 
 class Dpm:
@@ -279,3 +283,10 @@ class Dpm:
 
     def __exit__(self, *a):
         self.close()
+
+
+def dpm_load_phantom_raw(ctx, nx, ny, nz, dx, dy, dz, mat_ptr: int, rho_ptr: int) -> int:
+    """dpm_load_phantom from raw host pointers (e.g. pinned torch CPU tensors)."""
+    pid = C.c_int(-1)
+    _check(ctx, lib().dpm_load_phantom(ctx, nx, ny, nz, dx, dy, dz, _P(mat_ptr), _P(rho_ptr), C.byref(pid)))
+    return pid.value

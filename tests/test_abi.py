@@ -47,4 +47,4 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(dpm.dpm_material) == 4 + 4 + 3 * 8 * 8 + 8
     assert ctypes.sizeof(dpm.dpm_table_params) == 7 * 8 + 8
     assert ctypes.sizeof(dpm.dpm_source) == 8 + 8 + 3 * 8 + 4 * 8
-    assert ctypes.sizeof(dpm.dpm_run_opts) == 6 * 4 + 8
+    assert ctypes.sizeof(dpm.dpm_run_opts) == 6 * 4 + 8 + 8

@@ -1,0 +1,82 @@
+"""Error paths of the C ABI on the GPU: argument checks, call order, and the
+device-side bounded failures (queue overflow, wait time-out), which must
+return an error status and leave the context usable.  No test faults, traps
+or hangs the GPU: overflow and time-out are produced by tiny capacities and
+wait limits that the kernel checks itself."""
+import numpy as np
+import pytest
+
+from paper_0910_0329_gb300 import dpm
+from paper_0910_0329_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def code_of(fn, *a, **k):
+    with pytest.raises(dpm.DpmError) as e:
+        fn(*a, **k)
+    return e.value.code
+
+
+def test_argument_and_order_errors(gpu_lib):
+    wl = W.c1_photon_wbw()
+    ctx = dpm.dpm_create(0)
+    try:
+        pid = dpm.dpm_load_phantom(ctx, wl.phantom)
+        assert code_of(dpm.dpm_run, ctx, pid, wl.source, 0, 10, 1) == dpm.DPM_ESTATE  # no tables yet
+        dpm.dpm_build_tables(ctx, W.MATERIALS, wl.params)
+        assert code_of(dpm.dpm_run, ctx, 99, wl.source, 0, 10, 1) == dpm.DPM_EINVAL
+        bad = W.Source(W.ELECTRON, W.SPEC_MONO, 50.0, wl.source.iso)
+        assert code_of(dpm.dpm_run, ctx, pid, bad, 0, 10, 1) == dpm.DPM_EINVAL  # above e_max
+        assert code_of(dpm.dpm_run, ctx, pid, wl.source, 0, 10, 1, dpm.run_opts(n_batches=2000)) == dpm.DPM_EINVAL
+        assert code_of(dpm.dpm_run, ctx, pid, wl.source, 0, 10, 1, dpm.run_opts(physics_flags=8)) == dpm.DPM_EINVAL
+        assert code_of(dpm.dpm_run, ctx, pid, wl.source, 0, 10, 1, dpm.run_opts(queue_log2=3)) == dpm.DPM_EINVAL
+        ph = W.slab_phantom(2, 2, 2, 1.0, [(0, 1e9, 5, 1.0)])  # material 5 is beyond the 3 tables
+        pid2 = dpm.dpm_load_phantom(ctx, ph)
+        assert code_of(dpm.dpm_run, ctx, pid2, wl.source, 0, 10, 1) == dpm.DPM_EINVAL
+        bad_ph = W.slab_phantom(2, 2, 2, 1.0, [(0, 1e9, 0, 1.0)])
+        bad_ph.rho[3] = 0.0
+        assert code_of(dpm.dpm_load_phantom, ctx, bad_ph) == dpm.DPM_EINVAL
+        bad_ph.rho[3] = 1.0
+        bad_ph.nx = 3000
+        with pytest.raises((dpm.DpmError, ValueError)):
+            dpm.dpm_load_phantom(ctx, bad_ph)
+        p = dict(wl.params, n_e=10)
+        assert code_of(dpm.dpm_build_tables, ctx, W.MATERIALS, p) == dpm.DPM_EINVAL
+    finally:
+        dpm.dpm_destroy(ctx)
+
+
+def _ref_tally(wl, n):
+    with dpm.Dpm(0, W.MATERIALS, wl.params) as d:
+        pid = d.load_phantom(wl.phantom)
+        d.run(pid, wl.source, n, wl.seed, kernel=dpm.KERNEL_HISTORY)
+        return d.read(pid)[2]
+
+
+def test_queue_overflow_is_reported_and_recoverable():
+    wl = W.c1_photon_wbw()
+    with dpm.Dpm(0, W.MATERIALS, wl.params) as d:
+        pid = d.load_phantom(wl.phantom)
+        d.run(pid, wl.source, 400000, wl.seed, kernel=dpm.KERNEL_QUEUE, queue_log2=7, refill_min=1)
+        with pytest.raises(dpm.DpmError) as e:
+            d.read(pid)
+        assert e.value.code == dpm.DPM_EQUEUE_OVERFLOW
+        d.reset(pid)
+        d.run(pid, wl.source, 200000, wl.seed, kernel=dpm.KERNEL_QUEUE)
+        raw = d.read(pid)[2]
+    assert np.array_equal(raw, _ref_tally(wl, 200000))
+
+
+def test_wait_timeout_is_reported_and_recoverable():
+    wl = W.c0_electron_wlw()
+    with dpm.Dpm(0, W.MATERIALS, wl.params) as d:
+        pid = d.load_phantom(wl.phantom)
+        d.run(pid, wl.source, 20000, wl.seed, kernel=dpm.KERNEL_QUEUE, timeout_s=1e-7)
+        with pytest.raises(dpm.DpmError) as e:
+            d.read(pid)
+        assert e.value.code == dpm.DPM_ETIMEOUT
+        d.reset(pid)
+        d.run(pid, wl.source, 5000, wl.seed, kernel=dpm.KERNEL_QUEUE)
+        raw = d.read(pid)[2]
+    assert np.array_equal(raw, _ref_tally(wl, 5000))

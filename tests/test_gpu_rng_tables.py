@@ -46,58 +46,66 @@ def test_gpu_philox_bit_exact(tables_ctx):
         assert list(out[i]) == philox_ref(ctr[i].tolist(), key[i].tolist())
 
 
-# energies spanning the tables, avoiding one grid interval around the kinks of
-# the stopping power (T = 2 wcc, T = wcr) where linear interpolation is
-# first-order
-def energies(lo, hi, n=400, avoid=()):
-    e = np.geomspace(lo, hi, n)
-    keep = np.ones(n, bool)
-    for a in avoid:
-        keep &= np.abs(np.log(e / a)) > 0.01
-    return e[keep]
+def energies(lo, hi, n=400):
+    return np.geomspace(lo, hi, n)
 
 
 def mats():
     return [O.material(m) for m in W.MATERIALS]
 
 
-# Tolerances: linear interpolation on a ln E grid of spacing h = ln(e_hi/e_lo)/(n_e-1)
-# has relative error h^2/8 * |(ln f)''| + FP32 rounding; for these smooth
-# coefficients (powers up to E^-3) that is below 3e-5 at n_e = 2048.
-REL = 3e-5
+def grid(params=P):
+    """Energy nodes of the per-material tables (documented in include/dpm.h)."""
+    e_lo, e_hi = 0.99 * min(params["eabs_e"], params["eabs_g"]), 1.01 * params["e_max"]
+    return np.exp(np.linspace(np.log(e_lo), np.log(e_hi), int(params["n_e"])))
+
+
+def interp_tolerance(f, E, params=P):
+    """Bound on linear interpolation in ln E of the oracle function f at E: a
+    quarter of the largest second difference of f over the two node intervals
+    around E (h^2/8 f'' for smooth f, h/4 times the slope jump at a kink), plus
+    FP32 storage rounding."""
+    g = grid(params)
+    i = np.clip(np.searchsorted(g, E) - 1, 1, len(g) - 3)
+    f0, f1, f2, f3 = (np.array([f(g[j]) for j in i + k]) for k in (-1, 0, 1, 2))
+    d2 = np.maximum(np.abs(f2 - 2 * f1 + f0), np.abs(f3 - 2 * f2 + f1))
+    return d2 / 4.0 + 4e-7 * np.maximum(np.abs(f1), np.abs(f2))
+
+
+def check(got, f, E):
+    ref = np.array([f(e) for e in E])
+    tol = interp_tolerance(f, E)
+    bad = np.abs(got - ref) > tol
+    assert not bad.any(), list(zip(E[bad][:5], got[bad][:5], ref[bad][:5], tol[bad][:5]))
 
 
 @pytest.mark.parametrize("m", [0, 1, 2])
 def test_photon_coefficients(tables_ctx, m):
     L, mm = O.lib(), mats()[m]
     E = energies(0.051, 20.5)
-    mu = np.array([L.or_mu_compton(mm, e) + L.or_mu_photo(mm, e, P["c_pe"]) + L.or_mu_pair(mm, e) for e in E])
-    pc = np.array([L.or_mu_compton(mm, e) for e in E]) / mu
-    ppe = np.array([L.or_mu_photo(mm, e, P["c_pe"]) for e in E]) / mu
+    mc = lambda e: L.or_mu_compton(mm, e)
+    mp = lambda e: L.or_mu_photo(mm, e, P["c_pe"])
+    mt = lambda e: mc(e) + mp(e) + L.or_mu_pair(mm, e)
     ctx = tables_ctx.ctx
-    np.testing.assert_allclose(dpm.dpm_diag_table(ctx, 0, m, E), mu, rtol=REL)
-    np.testing.assert_allclose(dpm.dpm_diag_table(ctx, 1, m, E), pc, rtol=REL, atol=2e-6)
-    np.testing.assert_allclose(dpm.dpm_diag_table(ctx, 2, m, E), ppe, rtol=REL, atol=2e-6)
+    check(dpm.dpm_diag_table(ctx, 0, m, E), mt, E)
+    check(dpm.dpm_diag_table(ctx, 1, m, E), lambda e: mc(e) / mt(e), E)
+    check(dpm.dpm_diag_table(ctx, 2, m, E), lambda e: mp(e) / mt(e), E)
 
 
 @pytest.mark.parametrize("m", [0, 2])
 def test_electron_tables(tables_ctx, m):
     L, mm = O.lib(), mats()[m]
     pr = O.params(P)
-    E = energies(0.2, 20.5, avoid=(2 * P["wcc"], P["wcr"]))
+    E = energies(0.2, 20.5)
     ctx = tables_ctx.ctx
     e_lo = 0.99 * min(P["eabs_e"], P["eabs_g"])
-    S = np.array([L.or_scol(mm, e, P["wcc"]) + L.or_srad(mm, e, P["wcr"]) for e in E])
-    np.testing.assert_allclose(dpm.dpm_diag_table(ctx, 4, m, E), S, rtol=REL)
-    R = np.array([L.or_csda_path(mm, pr, e_lo, e) for e in E])
-    np.testing.assert_allclose(dpm.dpm_diag_table(ctx, 3, m, E), R, rtol=REL)
-    sm = np.array([L.or_moller_sigma(mm, e, P["wcc"]) for e in E])
-    sb = np.array([L.or_brems_sigma(mm, e, P["wcr"]) for e in E])
-    np.testing.assert_allclose(dpm.dpm_diag_table(ctx, 5, m, E), sm + sb, rtol=REL, atol=1e-7)
-    np.testing.assert_allclose(dpm.dpm_diag_table(ctx, 7, m, E), np.where(sm + sb > 0, sm / (sm + sb), 0),
-                               rtol=REL, atol=2e-6)
-    l1 = np.array([L.or_lambda1_inv(mm, e) for e in E])
-    np.testing.assert_allclose(dpm.dpm_diag_table(ctx, 6, m, E), l1, rtol=REL)
+    check(dpm.dpm_diag_table(ctx, 4, m, E), lambda e: L.or_scol(mm, e, P["wcc"]) + L.or_srad(mm, e, P["wcr"]), E)
+    check(dpm.dpm_diag_table(ctx, 3, m, E), lambda e: L.or_csda_path(mm, pr, e_lo, e), E)
+    sig = lambda e: L.or_moller_sigma(mm, e, P["wcc"]) + L.or_brems_sigma(mm, e, P["wcr"])
+    check(dpm.dpm_diag_table(ctx, 5, m, E), sig, E)
+    check(dpm.dpm_diag_table(ctx, 7, m, E), lambda e: L.or_moller_sigma(mm, e, P["wcc"]) / sig(e) if sig(e) > 0 else 0.0,
+          E)
+    check(dpm.dpm_diag_table(ctx, 6, m, E), lambda e: L.or_lambda1_inv(mm, e), E)
 
 
 @pytest.mark.parametrize("m", [0, 2])
@@ -107,7 +115,7 @@ def test_csda_energy_loss(tables_ctx, m):
     the 5 % energy-loss step."""
     L, mm = O.lib(), mats()[m]
     pr = O.params(P)
-    E = energies(0.21, 20.0, 200, avoid=(2 * P["wcc"],))
+    E = energies(0.21, 20.0, 200)
     path = np.array([L.or_csda_path(mm, pr, 0.95 * e, e) for e in E]) * np.linspace(0.02, 1.0, len(E))
     ref = np.array([L.or_csda_energy(mm, pr, e, s) for e, s in zip(E, path)])
     got = dpm.dpm_diag_table(tables_ctx.ctx, 8, m, E, path)
