@@ -36,7 +36,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--kernel", choices=["queue", "history"], default="history")
+    ap.add_argument("--kernel", choices=["queue", "history"], default="queue")
     ap.add_argument("--workload", default="6mv_wbw_61x61x60")
     ap.add_argument("--histories", type=int, default=0, help="histories per step (default: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -101,6 +101,28 @@ def measured_peaks():
             d = json.load(f)
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per history of `kernel` from the committed ncu summary, if the
+    kernel's source has not changed since the capture (else None)."""
+    import hashlib
+    import re
+
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    fp = re.search(r"first 16 hex digits\): `([0-9a-f]{16})`", text)
+    tb = re.search(r"traffic_bytes_per_history: ([0-9.]+)", text)
+    if not fp or not tb:
+        return None
+    src = os.path.join(ROOT, "paper_0910_0329_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("dpm_device.cuh", "dpm_queue.cu", "dpm_internal.h"):
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    return float(tb.group(1)) if h.hexdigest()[:16] == fp.group(1) else None
 
 
 def run_reference(args, rank):
@@ -172,7 +194,7 @@ def main():
     import numpy as np
     import torch
 
-    from paper_0910_0329_gb300 import build_lib, dpm
+    from paper_0910_0329_gb300 import build_lib, dpm, sharding
     from paper_0910_0329_gb300 import workloads as W
 
     build_lib.build()
@@ -187,7 +209,8 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
 
     def step(i):
-        d.run(pid, wl.source, n, wl.seed, first=(rank + world * i) * n, kernel=kernel)
+        first, _ = sharding.history_range(rank, world, i, n)
+        d.run(pid, wl.source, n, wl.seed, first=first, kernel=kernel)
 
     # warm-up
     for i in range(args.warmup):
@@ -245,8 +268,10 @@ def main():
     sec_per_hist = st["n_pushed"] / n_tot
     bytes_per_hist = 8 * atom_per_hist + 88 * sec_per_hist + 44
     achieved = bytes_per_hist * hist_per_launch / t_kernel_s / 1e9
+    kname = "k_queue" if kernel == dpm.KERNEL_QUEUE else "k_history"
+    tph = profiled_traffic(kname, args.workload)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_kind": peak_kind, "kernel": "k_queue" if kernel == dpm.KERNEL_QUEUE else "k_history",
+            "traffic": tph * hist_per_launch if tph else None, "peak_kind": peak_kind, "kernel": "k_queue" if kernel == dpm.KERNEL_QUEUE else "k_history",
             "kernel_ms_per_launch": t_kernel_s * 1000, "bytes_per_history": bytes_per_hist,
             "tally_atomics_per_history": atom_per_hist, "secondaries_per_history": sec_per_hist,
             "kernel_share_of_step": st["transport_ms"] / max(tot_ms, 1e-9)}

@@ -97,6 +97,8 @@ typedef struct {
     double timeout_s;  /* bound on any device wait (default 20 s) */
     int physics_flags; /* DPM_NO_HARD: no Moller/bremsstrahlung events; DPM_NO_MSC: no
                           elastic deflections (test and ablation switches; 0 = full physics) */
+    int queue_limit;   /* fault injection: largest occupancy of a queue shard (0 = capacity);
+                          a push that finds no shard below it is an overflow */
 } dpm_run_opts;
 enum { DPM_NO_HARD = 1, DPM_NO_MSC = 2 };
 

@@ -16,9 +16,11 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libdpm.so")
 
 CU = ["dpm_capi.cu", "dpm_history.cu", "dpm_queue.cu", "dpm_diag.cu"]
-CPP = ["dpm_tables.cpp"]
+CPP = ["dpm_tables.cpp", "dpm_host_tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INC]
+# -fmad=false: no implicit FMA contraction, so every kernel computes a particle
+# with the same rounding (explicit fmaf() where the code asks for fusion)
+NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-I" + INC]
 
 
 def _nvcc():
@@ -30,7 +32,7 @@ def _nvcc():
 
 
 def _sources():
-    deps = [os.path.join(SRC, f) for f in os.listdir(SRC)] + [os.path.join(INC, "dpm.h")]
+    deps = [os.path.join(SRC, f) for f in os.listdir(SRC)] + [os.path.join(INC, f) for f in os.listdir(INC)]
     return deps
 
 

@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "dpm_ctx.h"
 #include "dpm_internal.h"
 #include "dpm_kernels.h"
 #include "dpm_queue.h"
@@ -22,53 +23,10 @@ using namespace dpm;
 
 namespace {
 
-struct PhantomState {
-  int nx = 0, ny = 0, nz = 0;
-  double dx = 0, dy = 0, dz = 0;
-  size_t V = 0;
-  uint8_t *d_mat = nullptr;
-  float *d_rho = nullptr;
-  float *d_mumax = nullptr;
-  int mumax_version = -1;
-  int max_mat = 0;
-  double rho_max[DPM_MAX_MAT] = {0};
-  unsigned long long *d_slabs = nullptr;
-  size_t slab_batches = 0;
-  long long *d_S1 = nullptr;
-  double *d_Q = nullptr;
-  unsigned long long *d_counters = nullptr;
-  double *d_inv_nb = nullptr;
-  double *d_dose = nullptr, *d_sigma = nullptr;
-  uint64_t n_total = 0;
-  uint64_t b_total = 0;
-  // CUDA events around each transport launch and fold since the last read
-  std::vector<cudaEvent_t> ev;
-};
-
 void drop_events(PhantomState *p) {
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   p->ev.clear();
 }
-
-}  // namespace
-
-struct dpm_ctx {
-  int device = 0;
-  int sm_count = 0;
-  cudaStream_t own = nullptr, stream = nullptr;
-  std::string err;
-  bool tables_ready = false;
-  int tables_version = 0;
-  dpm_table_params params{};
-  HostTables ht;
-  DevTables dt{};
-  std::vector<void *> table_mem;
-  std::vector<std::unique_ptr<PhantomState>> phantoms;
-  int *d_err = nullptr;
-  QueueState queue;
-};
-
-namespace {
 
 int fail(dpm_ctx *c, int code, const std::string &msg) {
   if (c) c->err = msg;
@@ -134,7 +92,7 @@ int upload(dpm_ctx *c, const std::vector<T> &h, const T **out) {
 // Photon majorant of a phantom: for every energy node, the largest
 // rho * mu/rho over the materials present, at their largest density.
 int update_mumax(dpm_ctx *c, PhantomState *p) {
-  if (p->mumax_version == c->tables_version && p->d_mumax) return DPM_OK;
+  if (p->mumax_version == c->tables_version || !c->tables_ready) return DPM_OK;
   const HostTables &t = c->ht;
   std::vector<float> mm(t.n_e, 0.f);
   for (int i = 0; i < t.n_e; ++i) {
@@ -142,10 +100,6 @@ int update_mumax(dpm_ctx *c, PhantomState *p) {
     for (int m = 0; m <= p->max_mat && m < t.n_mat; ++m)
       if (p->rho_max[m] > 0) best = std::max(best, p->rho_max[m] * t.mu_mass_nodes[size_t(m) * t.n_e + i]);
     mm[i] = float(best * (1.0 + 1e-5));
-  }
-  if (!p->d_mumax) {
-    int rc = dalloc(c, &p->d_mumax, size_t(t.n_e));
-    if (rc) return rc;
   }
   CUDA_TRY(c, cudaMemcpy(p->d_mumax, mm.data(), mm.size() * sizeof(float), cudaMemcpyHostToDevice));
   p->mumax_version = c->tables_version;
@@ -160,6 +114,61 @@ uint64_t splitmix(uint64_t x) {
 }
 
 }  // namespace
+
+namespace dpm {
+
+int ctx_fail(dpm_ctx *c, int code, const std::string &msg) { return fail(c, code, msg); }
+
+PhantomState *ctx_phantom(dpm_ctx *c, int id) { return get_phantom(c, id); }
+
+int ctx_run_params(dpm_ctx *c, PhantomState *p, const dpm_source *src, uint64_t first, uint64_t n, uint64_t seed,
+                   int physics_flags, RunParams &R) {
+  if (!src) return fail(c, DPM_EINVAL, "null source");
+  if (!c->tables_ready) return fail(c, DPM_ESTATE, "dpm_build_tables() must precede dpm_run()");
+  if (p->max_mat >= c->ht.n_mat) return fail(c, DPM_EINVAL, "phantom uses a material index beyond the tables");
+  if (p->mumax_version != c->tables_version) return fail(c, DPM_ESTATE, "photon majorant is stale");
+  if (src->particle != 0 && src->particle != 1) return fail(c, DPM_EINVAL, "particle must be 0 or 1");
+  if (src->spectrum != 0 && src->spectrum != 1) return fail(c, DPM_EINVAL, "spectrum must be 0 or 1");
+  const double emax = src->spectrum == 1 ? 6.0 : src->energy;
+  if (!(emax > 0) || emax > c->params.e_max) return fail(c, DPM_EINVAL, "source energy outside (0, e_max]");
+  if (!(src->sad > 0) || !(src->fx >= 0) || !(src->fy >= 0)) return fail(c, DPM_EINVAL, "bad beam geometry");
+  if (n > 0xFFFFFFFFull) return fail(c, DPM_EINVAL, "at most 2^32-1 histories per call");
+  if (physics_flags & ~(DPM_NO_HARD | DPM_NO_MSC)) return fail(c, DPM_EINVAL, "unknown physics flag");
+  R.T = c->dt;
+  R.T.flags = physics_flags;
+  R.P.nx = p->nx;
+  R.P.ny = p->ny;
+  R.P.nz = p->nz;
+  R.P.dx = float(p->dx);
+  R.P.dy = float(p->dy);
+  R.P.dz = float(p->dz);
+  R.P.mat = p->d_mat;
+  R.P.rho = p->d_rho;
+  R.P.mu_max = p->d_mumax;
+  const double g = src->gantry_deg * 3.14159265358979323846 / 180.0;
+  const double ax[3] = {std::sin(g), 0.0, std::cos(g)};
+  R.S.particle = src->particle;
+  R.S.spectrum = src->spectrum;
+  R.S.energy = float(src->energy);
+  R.S.sx = float(src->iso[0] - src->sad * ax[0]);
+  R.S.sy = float(src->iso[1] - src->sad * ax[1]);
+  R.S.sz = float(src->iso[2] - src->sad * ax[2]);
+  R.S.cx = float(src->iso[0]);
+  R.S.cy = float(src->iso[1]);
+  R.S.cz = float(src->iso[2]);
+  R.S.e1x = float(std::cos(g));
+  R.S.e1z = float(-std::sin(g));
+  R.S.fx = float(src->fx);
+  R.S.fy = float(src->fy);
+  R.first = first;
+  R.n = n;
+  const uint64_t k = splitmix(seed);
+  R.key0 = uint32_t(k);
+  R.key1 = uint32_t(k >> 32);
+  return DPM_OK;
+}
+
+}  // namespace dpm
 
 extern "C" {
 
@@ -228,7 +237,7 @@ int dpm_load_phantom(dpm_ctx *c, int nx, int ny, int nz, double dx, double dy, d
   int rc;
   if ((rc = dalloc(c, &p->d_mat, p->V)) || (rc = dalloc(c, &p->d_rho, p->V)) || (rc = dalloc(c, &p->d_S1, p->V)) ||
       (rc = dalloc(c, &p->d_Q, p->V)) || (rc = dalloc(c, &p->d_counters, size_t(C_N))) ||
-      (rc = dalloc(c, &p->d_inv_nb, size_t(1024)))) {
+      (rc = dalloc(c, &p->d_inv_nb, size_t(1024))) || (rc = dalloc(c, &p->d_mumax, size_t(kMaxTableNodes)))) {
     free_phantom(p.get());
     return rc;
   }
@@ -238,6 +247,10 @@ int dpm_load_phantom(dpm_ctx *c, int nx, int ny, int nz, double dx, double dy, d
   CUDA_TRY(c, cudaMemsetAsync(p->d_Q, 0, p->V * sizeof(double), c->stream));
   CUDA_TRY(c, cudaMemsetAsync(p->d_counters, 0, C_N * sizeof(unsigned long long), c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if ((rc = update_mumax(c, p.get()))) {
+    free_phantom(p.get());
+    return rc;
+  }
   c->phantoms.push_back(std::move(p));
   *phantom_id = int(c->phantoms.size()) - 1;
   return DPM_OK;
@@ -298,6 +311,8 @@ int dpm_build_tables(dpm_ctx *c, const dpm_material *mats, int n_mat, const dpm_
   c->params = *p;
   c->tables_ready = true;
   c->tables_version++;
+  for (auto &ph : c->phantoms)
+    if (ph && (rc = update_mumax(c, ph.get()))) return rc;
   return DPM_OK;
 }
 
@@ -319,28 +334,20 @@ int dpm_reset_tally(dpm_ctx *c, int id) {
 int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t n, uint64_t seed,
             const dpm_run_opts *opts) {
   if (!c) return DPM_EINVAL;
-  if (!src) return fail(c, DPM_EINVAL, "null source");
-  if (!c->tables_ready) return fail(c, DPM_ESTATE, "dpm_build_tables() must precede dpm_run()");
   PhantomState *p = get_phantom(c, id);
   if (!p) return fail(c, DPM_EINVAL, "bad phantom id");
-  if (p->max_mat >= c->ht.n_mat) return fail(c, DPM_EINVAL, "phantom uses a material index beyond the tables");
-  if (src->particle != 0 && src->particle != 1) return fail(c, DPM_EINVAL, "particle must be 0 or 1");
-  if (src->spectrum != 0 && src->spectrum != 1) return fail(c, DPM_EINVAL, "spectrum must be 0 or 1");
-  const double emax = src->spectrum == 1 ? 6.0 : src->energy;
-  if (!(emax > 0) || emax > c->params.e_max) return fail(c, DPM_EINVAL, "source energy outside (0, e_max]");
-  if (!(src->sad > 0) || !(src->fx >= 0) || !(src->fy >= 0)) return fail(c, DPM_EINVAL, "bad beam geometry");
-  if (n > 0xFFFFFFFFull) return fail(c, DPM_EINVAL, "at most 2^32-1 histories per call");
-  if (n == 0) return DPM_OK;
   dpm_run_opts o{};
   if (opts) o = *opts;
+  RunParams R{};
+  int rc = ctx_run_params(c, p, src, first, n, seed, o.physics_flags, R);
+  if (rc) return rc;
+  if (n == 0) return DPM_OK;
   int nb = o.n_batches > 0 ? o.n_batches : 50;
   if (nb > 1024) return fail(c, DPM_EINVAL, "n_batches must be <= 1024");
   if (uint64_t(nb) > n) nb = int(n);
   const uint64_t bs = (n + nb - 1) / nb;
   const int B = int((n + bs - 1) / bs);
   cudaSetDevice(c->device);
-  int rc = update_mumax(c, p);
-  if (rc) return rc;
   if (p->slab_batches < size_t(B)) {
     cudaFree(p->d_slabs);
     p->d_slabs = nullptr;
@@ -352,36 +359,6 @@ int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t 
   for (int b = 0; b < B; ++b) inv_nb[b] = 1.0 / double(std::min<uint64_t>(bs, n - uint64_t(b) * bs));
   CUDA_TRY(c, cudaMemcpyAsync(p->d_inv_nb, inv_nb.data(), B * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(p->d_slabs, 0, size_t(B) * p->V * sizeof(unsigned long long), c->stream));
-
-  if (o.physics_flags & ~(DPM_NO_HARD | DPM_NO_MSC)) return fail(c, DPM_EINVAL, "unknown physics flag");
-  RunParams R{};
-  R.T = c->dt;
-  R.T.flags = o.physics_flags;
-  R.P.nx = p->nx; R.P.ny = p->ny; R.P.nz = p->nz;
-  R.P.dx = float(p->dx); R.P.dy = float(p->dy); R.P.dz = float(p->dz);
-  R.P.mat = p->d_mat;
-  R.P.rho = p->d_rho;
-  R.P.mu_max = p->d_mumax;
-  const double g = src->gantry_deg * 3.14159265358979323846 / 180.0;
-  const double ax[3] = {std::sin(g), 0.0, std::cos(g)};
-  R.S.particle = src->particle;
-  R.S.spectrum = src->spectrum;
-  R.S.energy = float(src->energy);
-  R.S.sx = float(src->iso[0] - src->sad * ax[0]);
-  R.S.sy = float(src->iso[1] - src->sad * ax[1]);
-  R.S.sz = float(src->iso[2] - src->sad * ax[2]);
-  R.S.cx = float(src->iso[0]);
-  R.S.cy = float(src->iso[1]);
-  R.S.cz = float(src->iso[2]);
-  R.S.e1x = float(std::cos(g));
-  R.S.e1z = float(-std::sin(g));
-  R.S.fx = float(src->fx);
-  R.S.fy = float(src->fy);
-  R.first = first;
-  R.n = n;
-  const uint64_t k = splitmix(seed);
-  R.key0 = uint32_t(k);
-  R.key1 = uint32_t(k >> 32);
   R.n_batches = B;
   R.slabs = p->d_slabs;
   R.counters = p->d_counters;

@@ -1,0 +1,68 @@
+// dpm_ctx.h -- library-internal definition of the context behind the C ABI
+// (shared by the translation units that implement ABI calls).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "dpm_internal.h"
+#include "dpm_queue.h"
+
+namespace dpm {
+
+constexpr int kMaxTableNodes = 65536;  // upper bound of dpm_table_params.n_e
+
+struct PhantomState {
+  int nx = 0, ny = 0, nz = 0;
+  double dx = 0, dy = 0, dz = 0;
+  size_t V = 0;
+  uint8_t *d_mat = nullptr;
+  float *d_rho = nullptr;
+  float *d_mumax = nullptr;  // kMaxTableNodes floats, filled for the current tables
+  int mumax_version = -1;
+  int max_mat = 0;
+  double rho_max[DPM_MAX_MAT] = {0};
+  unsigned long long *d_slabs = nullptr;
+  size_t slab_batches = 0;
+  long long *d_S1 = nullptr;
+  double *d_Q = nullptr;
+  unsigned long long *d_counters = nullptr;
+  double *d_inv_nb = nullptr;
+  double *d_dose = nullptr, *d_sigma = nullptr;
+  uint64_t n_total = 0;
+  uint64_t b_total = 0;
+  // CUDA events around each transport launch and fold since the last read
+  std::vector<cudaEvent_t> ev;
+};
+
+}  // namespace dpm
+
+struct dpm_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t own = nullptr, stream = nullptr;
+  std::string err;
+  bool tables_ready = false;
+  int tables_version = 0;
+  dpm_table_params params{};
+  dpm::HostTables ht;
+  dpm::DevTables dt{};
+  std::vector<void *> table_mem;
+  std::vector<std::unique_ptr<dpm::PhantomState>> phantoms;
+  int *d_err = nullptr;
+  dpm::QueueState queue;
+};
+
+namespace dpm {
+
+int ctx_fail(dpm_ctx *c, int code, const std::string &msg);
+PhantomState *ctx_phantom(dpm_ctx *c, int id);
+// Validate a run request and fill the launch parameters (tally pointers and
+// batch size are left to the caller).  Allocates nothing.
+int ctx_run_params(dpm_ctx *c, PhantomState *p, const dpm_source *src, uint64_t first, uint64_t n, uint64_t seed,
+                   int physics_flags, RunParams &R);
+
+}  // namespace dpm

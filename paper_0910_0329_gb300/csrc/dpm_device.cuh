@@ -23,6 +23,16 @@ constexpr int kMaxElectronSteps = 200000;  // per particle; far above any real t
 constexpr int kMaxPhotonFlights = 100000;
 constexpr int kMaxPhotonSegments = 10000;  // Compton scatters of one photon
 
+// Rarely executed physics (source, interactions, hard events, annihilation)
+// is inlined: measured on GB300, calls to out-of-line copies cost more than
+// the instruction-cache pressure they save.  DPM_COLD_NOINLINE keeps it out
+// of line (for measurements).
+#ifdef DPM_COLD_NOINLINE
+#define DPM_COLD __noinline__
+#else
+#define DPM_COLD __forceinline__
+#endif
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): counter-based, so a particle's random
 // numbers depend only on its identity, never on the thread that runs it.
@@ -134,12 +144,13 @@ __device__ __forceinline__ void locate(Part &p, const DevPhantom &P) {
   p.iz = min(max(int(floorf(p.z / P.dz)), 0), P.nz - 1);
 }
 
-// Rotate the direction by polar cosine c and azimuth phi.
-__device__ __forceinline__ void rotate(float &u, float &v, float &w, float c, float phi) {
+// Rotate the direction by polar cosine c and azimuth pi*h (h in half turns,
+// so that sincospif's exact argument reduction applies).
+__device__ __forceinline__ void rotate(float &u, float &v, float &w, float c, float h) {
   c = fminf(fmaxf(c, -1.f), 1.f);
   const float s = sqrtf(fmaxf(0.f, 1.f - c * c));
   float sp, cp;
-  sincosf(phi, &sp, &cp);
+  sincospif(h, &sp, &cp);
   const float r2 = u * u + v * v;
   float nu, nv, nw;
   if (r2 < 1e-10f) {
@@ -255,12 +266,12 @@ __device__ __forceinline__ float spectrum_6mv(float u) {
 // spot (Sec. 3); a positron then also annihilates.
 // ---------------------------------------------------------------------------
 template <class Sink>
-__device__ void annihilate(Part &p, const RunParams &R, Sink &s) {
+__device__ DPM_COLD void annihilate(Part &p, const RunParams &R, Sink &s) {
   const uint4 r = draw(p, R);
-  const float cz = 2.f * u01(r.x) - 1.f, phi = kTwoPi * u01(r.y);
+  const float cz = 2.f * u01(r.x) - 1.f;
   const float sz = sqrtf(fmaxf(0.f, 1.f - cz * cz));
   float sp, cp;
-  sincosf(phi, &sp, &cp);
+  sincospif(2.f * u01(r.y), &sp, &cp);
   Part g = child(p, PHOTON, 1);
   g.E = kMc2f;
   g.u = sz * cp;
@@ -302,7 +313,7 @@ __device__ void absorb_charged(Part &p, const RunParams &R, Sink &s) {
 // field rectangle in the isocentre plane, flown to the phantom surface.
 // Returns false if the ray misses the phantom.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool make_primary(Part &p, const RunParams &R, uint32_t hl) {
+static __device__ DPM_COLD bool make_primary(Part &p, const RunParams &R, uint32_t hl) {
   const DevSource &S = R.S;
   const DevPhantom &P = R.P;
   p.hist = hl;
@@ -352,7 +363,7 @@ __device__ __forceinline__ bool make_primary(Part &p, const RunParams &R, uint32
 // Returns true while the photon is alive (after a Compton scatter).
 // ---------------------------------------------------------------------------
 template <class Sink>
-__device__ bool photon_interact(Part &p, const RunParams &R, Sink &s, EIdx e, int m) {
+__device__ DPM_COLD bool photon_interact(Part &p, const RunParams &R, Sink &s, EIdx e, int m) {
   const DevTables &T = R.T;
   const uint4 r = draw(p, R);
   const float4 c = ph_at(T, m, e);
@@ -391,14 +402,14 @@ __device__ bool photon_interact(Part &p, const RunParams &R, Sink &s, EIdx e, in
   const float eps = expf(samp(T.kn, lnE, u01(r.y)) * l0);
   const float Ep = eps * E, Te = E - Ep;
   const float cth = 1.f - (1.f / eps - 1.f) / k;
-  const float phi = kTwoPi * u01(r.z);
+  const float h = 2.f * u01(r.z);  // azimuth in half turns
   Part el = child(p, ELECTRON, 1);
   el.E = Te;
   const float pe = sqrtf(Te * (Te + 2.f * kMc2f));
   const float ce = pe > 0.f ? (E - Ep * cth) / pe : 1.f;
-  rotate(el.u, el.v, el.w, ce, phi + kPif);
+  rotate(el.u, el.v, el.w, ce, h + 1.f);
   emit_charged(el, R, s);
-  rotate(p.u, p.v, p.w, cth, phi);
+  rotate(p.u, p.v, p.w, cth, h);
   p.E = Ep;
   if (Ep <= T.eabs_g) {
     s.deposit(vox(p, R.P), Ep);
@@ -450,7 +461,7 @@ __device__ bool photon_segment(Part &p, const RunParams &R, Sink &s) {
 // Returns true while the particle is alive.
 // ---------------------------------------------------------------------------
 template <class Sink>
-__device__ void electron_hard(Part &p, const RunParams &R, Sink &s, float sig0, int m) {
+__device__ DPM_COLD void electron_hard(Part &p, const RunParams &R, Sink &s, float sig0, int m) {
   const DevTables &T = R.T;
   const uint4 r = draw(p, R);
   const float Tn = p.E;
@@ -460,7 +471,7 @@ __device__ void electron_hard(Part &p, const RunParams &R, Sink &s, float sig0, 
   const float pm = lerp(__ldg(T.pmol + size_t(m) * T.n_e + e.i), __ldg(T.pmol + size_t(m) * T.n_e + e.i + 1), e.f);
   const float lnT = logf(Tn);
   const float ec = T.wcc / Tn;
-  const float phi = kTwoPi * u01(r.w);
+  const float h = 2.f * u01(r.w);  // azimuth in half turns
   if (u01(r.y) < pm && ec < 0.5f) {
     // Moller: z = (1/ec - 1/eps)/(1/ec - 2)
     const float z = samp(T.mol, lnT, u01(r.z));
@@ -470,9 +481,9 @@ __device__ void electron_hard(Part &p, const RunParams &R, Sink &s, float sig0, 
     const float cpr = sqrtf(Tp * (Tn + 2.f * kMc2f) / (Tn * (Tp + 2.f * kMc2f)));
     Part d = child(p, ELECTRON, 1);
     d.E = W;
-    rotate(d.u, d.v, d.w, cs, phi);
+    rotate(d.u, d.v, d.w, cs, h);
     emit_charged(d, R, s);
-    rotate(p.u, p.v, p.w, cpr, phi + kPif);
+    rotate(p.u, p.v, p.w, cpr, h + 1.f);
     p.E = Tp;
   } else if (Tn > T.wcr) {
     // bremsstrahlung photon along the electron: y = ln(k/wcr)/ln(T/wcr)
@@ -521,7 +532,7 @@ __device__ bool electron_step(Part &p, const RunParams &R, Sink &s) {
     if (!(T.flags & DPM_NO_MSC)) {
       const float A = msc_A(T, rho * st * r0.w);
       const float omc = msc_sample(A, u01(rn.z));
-      rotate(p.u, p.v, p.w, 1.f - omc, kTwoPi * u01(rn.w));
+      rotate(p.u, p.v, p.w, 1.f - omc, 2.f * u01(rn.w));
     }
     const float rest = st - th;
     const float t2 = dist_to_face(p, P, axis);

@@ -76,7 +76,7 @@ __device__ void reduce_counters(const long long *cnt, int err, const RunParams &
 
 constexpr int kHistStack = 64;
 
-__global__ void __launch_bounds__(128) k_history(RunParams R, uint64_t batch_size) {
+__global__ void __launch_bounds__(128) k_history(const __grid_constant__ RunParams R, uint64_t batch_size) {
   Part stack[kHistStack];
   HistSink s(R, stack, kHistStack);
   const size_t V = size_t(R.P.nx) * R.P.ny * R.P.nz;
@@ -125,6 +125,7 @@ void launch_history(const RunParams &R, uint64_t batch_size, int sm_count, int b
   const uint64_t need = (R.n + block - 1) / block;
   const uint64_t cap = uint64_t(sm_count) * 16;
   const int grid = int(need < cap ? need : cap);
+  cudaFuncSetAttribute(k_history, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   k_history<<<grid > 0 ? grid : 1, block, 0, st>>>(R, batch_size);
 }
 

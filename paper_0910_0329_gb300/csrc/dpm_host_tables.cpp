@@ -3,6 +3,7 @@
 // logic).  Not part of the device path.
 #include <cstring>
 
+#include "dpm_host.h"
 #include "dpm_internal.h"
 
 extern "C" {

@@ -30,6 +30,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kQBlock = 128;
 constexpr int kStealProbes = 8;
+constexpr int kSpillProbes = 8;
 
 struct alignas(128) Ctl {
   unsigned long long v;
@@ -49,6 +50,7 @@ struct QDev {
   Ctl *next_hist, *idle, *started;
   int refill_min;
   uint32_t high_water;
+  uint32_t limit;  // pushes beyond this occupancy of a shard spill over (fault injection can lower it)
   unsigned long long timeout_ns;   // bound on any single wait
   unsigned long long deadline_ns;  // bound on the whole launch (from kernel start)
   uint64_t batch_size;
@@ -122,7 +124,7 @@ struct QSink {
   // Warp-aggregated push of the lanes that are here together: one atomic on
   // the shard's tail per queue type, then each lane writes its record and
   // publishes its slot.
-  __device__ void push(const Part &q) {
+  __device__ DPM_COLD void push(const Part &q) {
     ++cnt[C_PUSH];
     const int t = (q.type == PHOTON) ? 0 : 1;
     const unsigned act = __activemask();
@@ -140,24 +142,30 @@ struct QSink {
     const int rank = __popc(mask & lanemask_lt());
     const QType &Qt = Q.q[t];
     unsigned long long base = 0;
-    int room = 1;
+    int shard = -1;
     if ((int)(threadIdx.x & 31) == leader) {
-      const unsigned long long h = ld_volatile(&Qt.head[home].v);
-      const unsigned long long tl = ld_volatile(&Qt.tail[home].v);
-      const unsigned long long cap = 1ull << Q.log2cs;
-      if (occupancy(h, tl) + __popc(mask) > cap - 64) room = 0;
-      else base = atomicAdd(&Qt.tail[home].v, (unsigned long long)__popc(mask));
+      // the CTA's own shard, else the next ones (a full shard spills over)
+      for (int k = 0; k <= kSpillProbes && k < Q.K; ++k) {
+        const int s = (home + k) % Q.K;
+        const unsigned long long h = ld_volatile(&Qt.head[s].v);
+        const unsigned long long tl = ld_volatile(&Qt.tail[s].v);
+        if (occupancy(h, tl) + __popc(mask) <= Q.limit) {
+          base = atomicAdd(&Qt.tail[s].v, (unsigned long long)__popc(mask));
+          shard = s;
+          break;
+        }
+      }
     }
     base = __shfl_sync(mask, base, leader);
-    room = __shfl_sync(mask, room, leader);
-    if (!room) {
+    shard = __shfl_sync(mask, shard, leader);
+    if (shard < 0) {
       err |= ERR_OVERFLOW;
       cnt[C_ESC] += fx(q.E + (q.type == POSITRON ? 2.f * kMc2f : 0.f));
       return;
     }
     const unsigned long long p = base + rank;
     const uint32_t slot = uint32_t(p) & Q.mask;
-    const size_t idx = (size_t(home) << Q.log2cs) + slot;
+    const size_t idx = (size_t(shard) << Q.log2cs) + slot;
     // wait for the consumer of position p - capacity to have freed the slot
     if (ld_volatile32(Qt.seq + idx) != uint32_t(p)) {
       const unsigned long long t0 = now_ns();
@@ -274,8 +282,8 @@ __device__ int refill_source(const RunParams &R, const QDev &Q, unsigned empty, 
   const int want = __popc(empty);
   if (want == 0) return 0;
   const int lane = threadIdx.x & 31;
-  unsigned long long b = 0;
-  if (lane == 0) b = atomicAdd(&Q.next_hist->v, (unsigned long long)want);
+  unsigned long long b = R.n;
+  if (lane == 0 && ld_volatile(&Q.next_hist->v) < R.n) b = atomicAdd(&Q.next_hist->v, (unsigned long long)want);
   b = __shfl_sync(kFull, b, 0);
   if (b >= R.n) return 0;
   if (empty & (1u << lane)) {
@@ -300,12 +308,12 @@ __device__ bool any_work(const RunParams &R, const QDev &Q) {
   return __any_sync(kFull, w);
 }
 
+// False while either of the CTA's shards is above its high-water mark.
 __device__ bool source_allowed(const RunParams &R, const QDev &Q, int home) {
   bool ok = true;
   if ((threadIdx.x & 31) == 0) {
     for (int t = 0; t < 2; ++t)
       if (occupancy(ld_volatile(&Q.q[t].head[home].v), ld_volatile(&Q.q[t].tail[home].v)) > Q.high_water) ok = false;
-    if (ld_volatile(&Q.next_hist->v) >= R.n) ok = false;
   }
   return __shfl_sync(kFull, ok, 0);
 }
@@ -324,7 +332,12 @@ __device__ void reduce_counters_q(const long long *cnt, int err, const RunParams
   if ((threadIdx.x & 31) == 0 && e) atomicOr(R.err, e);
 }
 
-__global__ void __launch_bounds__(kQBlock) k_queue(RunParams R, QDev Q) {
+// Eight resident blocks per SM caps the kernel at 64 registers per thread:
+// 32 warps per SM, the fastest of the register/occupancy trade-offs measured.
+#ifndef DPM_QUEUE_MIN_BLOCKS
+#define DPM_QUEUE_MIN_BLOCKS 8
+#endif
+__global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS) k_queue(const __grid_constant__ RunParams R, const __grid_constant__ QDev Q) {
   const int lane = threadIdx.x & 31;
   const int home = blockIdx.x % Q.K;
   const int src_type = (R.S.particle == 0) ? 0 : 1;
@@ -354,7 +367,9 @@ __global__ void __launch_bounds__(kQBlock) k_queue(RunParams R, QDev Q) {
         else if (refill_queue(Q, 1, home, kStealProbes, empty, p, alive, sk.err)) mode = 1;
         else if (refill_queue(Q, 0, home, kStealProbes, empty, p, alive, sk.err)) mode = 0;
       } else if (mode == src_type) {
-        if (!refill_queue(Q, mode, home, 0, empty, p, alive, sk.err) && source_allowed(R, Q, home))
+        // while the CTA's shards are filling up, let these lanes drain so
+        // that the warp turns to the secondaries
+        if (source_allowed(R, Q, home) && !refill_queue(Q, mode, home, 0, empty, p, alive, sk.err))
           refill_source(R, Q, empty, p, alive, sk);
       } else {
         refill_queue(Q, mode, home, kStealProbes, empty, p, alive, sk.err);
@@ -431,48 +446,31 @@ __global__ void k_queue_init(uint32_t *seq0, uint32_t *seq1, size_t n, uint32_t 
 
 }  // namespace
 
-int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_run_opts &o, int sm_count,
-              cudaStream_t st, cudaEvent_t start, std::string &err) {
-  if (R.n > 0x7fffffffull) {
-    err = "the queue kernel takes at most 2^31-1 histories per call";
-    return DPM_EINVAL;
-  }
+int queue_blocks_per_sm() {
+  // the kernel keeps no shared memory: give the whole carveout to L1, where
+  // the tables are cached
+  cudaFuncSetAttribute(k_queue, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_queue, kQBlock, 0);
-  if (e != cudaSuccess || per_sm < 1) {
-    err = std::string("occupancy query failed: ") + cudaGetErrorString(e);
-    return DPM_ECUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_queue, kQBlock, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
   }
-  if (o.block_size != 0 && o.block_size != kQBlock) {
-    // the block shape is fixed by the kernel's launch bound; more warps per SM
-    // come from more blocks
-  }
-  int bps = o.blocks_per_sm > 0 ? std::min(o.blocks_per_sm, per_sm) : per_sm;
-  const int K = sm_count * bps;
-  const int log2cs = o.queue_log2 > 0 ? o.queue_log2 : 13;
-  if (log2cs < 7 || log2cs > 20) {
-    err = "queue_log2 must be in [7, 20]";
-    return DPM_EINVAL;
-  }
+  return per_sm;
+}
+
+size_t queue_bytes(int K, int log2cs) {
+  const size_t slots = size_t(K) << log2cs;
+  const size_t per_type = slots * 12 * sizeof(uint32_t) + 2 * size_t(K) * sizeof(Ctl);
+  return 2 * per_type + 3 * sizeof(Ctl) + 128;
+}
+
+int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batch_size, const dpm_run_opts &o,
+                 int sm_count, cudaStream_t st, cudaEvent_t start, std::string &err) {
   const size_t cs = size_t(1) << log2cs;
   const size_t slots = size_t(K) * cs;
   const size_t per_type = slots * 12 * sizeof(uint32_t) + 2 * size_t(K) * sizeof(Ctl);
-  const size_t bytes = 2 * per_type + 3 * sizeof(Ctl) + 256;
-  if (q.bytes < bytes) {
-    if (q.mem) cudaFree(q.mem);
-    q.mem = nullptr;
-    q.bytes = 0;
-    e = cudaMalloc(&q.mem, bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      err = std::string("queue allocation: ") + cudaGetErrorString(e);
-      return DPM_ENOMEM;
-    }
-    q.bytes = bytes;
-  }
-  q.log2_cap = log2cs;
   QDev Q{};
-  char *m = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(q.mem) + 127) & ~uintptr_t(127));
+  char *m = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(mem) + 127) & ~uintptr_t(127));
   Q.next_hist = reinterpret_cast<Ctl *>(m);
   Q.idle = Q.next_hist + 1;
   Q.started = Q.next_hist + 2;
@@ -496,6 +494,8 @@ int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_
   Q.mask = uint32_t(cs - 1);
   Q.refill_min = o.refill_min > 0 ? std::min(o.refill_min, 32) : 8;
   Q.high_water = uint32_t(cs / 4);
+  Q.limit = uint32_t(cs - 64);
+  if (o.queue_limit > 0) Q.limit = std::min<uint32_t>(Q.limit, uint32_t(o.queue_limit));
   const double tmo = o.timeout_s > 0 ? o.timeout_s : 20.0;
   Q.timeout_ns = (unsigned long long)(tmo * 1e9);
   // the whole launch: the wait bound plus 2 us per history (a hundred times the
@@ -503,15 +503,14 @@ int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_
   Q.deadline_ns = Q.timeout_ns + (unsigned long long)(double(R.n) * 2000.0);
   Q.batch_size = batch_size;
   // zero the control words of both types and the three run counters
-  e = cudaMemsetAsync(m, 0, 3 * sizeof(Ctl), st);
-  for (int t = 0; t < 2 && e == cudaSuccess; ++t)
-    e = cudaMemsetAsync(Q.q[t].head, 0, 2 * size_t(K) * sizeof(Ctl), st);
+  cudaError_t e = cudaMemsetAsync(m, 0, 3 * sizeof(Ctl), st);
+  for (int t = 0; t < 2 && e == cudaSuccess; ++t) e = cudaMemsetAsync(Q.q[t].head, 0, 2 * size_t(K) * sizeof(Ctl), st);
   if (e != cudaSuccess) {
     err = cudaGetErrorString(e);
     return DPM_ECUDA;
   }
   k_queue_init<<<sm_count * 4, 256, 0, st>>>(Q.q[0].seq, Q.q[1].seq, slots, Q.mask);
-  cudaEventRecord(start, st);
+  if (start) cudaEventRecord(start, st);
   k_queue<<<K, kQBlock, 0, st>>>(R, Q);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -519,6 +518,41 @@ int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_
     return DPM_ECUDA;
   }
   return DPM_OK;
+}
+
+int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_run_opts &o, int sm_count,
+              cudaStream_t st, cudaEvent_t start, std::string &err) {
+  if (R.n > 0x7fffffffull) {
+    err = "the queue kernel takes at most 2^31-1 histories per call";
+    return DPM_EINVAL;
+  }
+  const int per_sm = queue_blocks_per_sm();
+  if (per_sm < 1) {
+    err = "occupancy query failed";
+    return DPM_ECUDA;
+  }
+  const int bps = o.blocks_per_sm > 0 ? std::min(o.blocks_per_sm, per_sm) : per_sm;
+  const int K = sm_count * bps;
+  const int log2cs = o.queue_log2 > 0 ? o.queue_log2 : 14;
+  if (log2cs < 7 || log2cs > 20) {
+    err = "queue_log2 must be in [7, 20]";
+    return DPM_EINVAL;
+  }
+  const size_t bytes = queue_bytes(K, log2cs);
+  if (q.bytes < bytes) {
+    if (q.mem) cudaFree(q.mem);
+    q.mem = nullptr;
+    q.bytes = 0;
+    cudaError_t e = cudaMalloc(&q.mem, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      err = std::string("queue allocation: ") + cudaGetErrorString(e);
+      return DPM_ENOMEM;
+    }
+    q.bytes = bytes;
+  }
+  q.log2_cap = log2cs;
+  return queue_launch(q.mem, K, log2cs, R, batch_size, o, sm_count, st, start, err);
 }
 
 void queue_free(QueueState &q) {

@@ -16,9 +16,18 @@ struct QueueState {
 };
 
 // Launch the persistent kernel for one run; returns a dpm_status code.
-// `start` is recorded on the stream just before the transport kernel.
+// `start` (may be NULL) is recorded on the stream just before the transport kernel.
 int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_run_opts &o, int sm_count,
               cudaStream_t st, cudaEvent_t start, std::string &err);
 void queue_free(QueueState &q);
+
+// Resident blocks per SM of the queue kernel (occupancy query), or 0 on error.
+int queue_blocks_per_sm();
+// Device bytes the queues of K shards of 2^log2cs slots occupy.
+size_t queue_bytes(int K, int log2cs);
+// Lay the queues out in caller-provided device memory `mem` (at least
+// queue_bytes(K, log2cs) bytes, any alignment) and launch: allocates nothing.
+int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batch_size, const dpm_run_opts &o,
+                 int sm_count, cudaStream_t st, cudaEvent_t start, std::string &err);
 
 }  // namespace dpm

@@ -49,7 +49,7 @@ class dpm_source(C.Structure):
 class dpm_run_opts(C.Structure):
     _fields_ = [("kernel", C.c_int), ("n_batches", C.c_int), ("block_size", C.c_int), ("blocks_per_sm", C.c_int),
                 ("queue_log2", C.c_int), ("refill_min", C.c_int), ("timeout_s", C.c_double),
-                ("physics_flags", C.c_int)]
+                ("physics_flags", C.c_int), ("queue_limit", C.c_int)]
 
 
 class dpm_run_stats(C.Structure):
@@ -83,6 +83,10 @@ _SIGS = {
     "dpm_diag_table": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
     "dpm_diag_sample": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, _P, _P]),
     "dpm_diag_philox": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    # include/dpm_host.h (host-only table inspection)
+    "dpm_host_tables_build": (_P, [C.POINTER(dpm_material), C.c_int, C.POINTER(dpm_table_params), C.c_char_p]),
+    "dpm_host_tables_free": (None, [_P]),
+    "dpm_host_tables_get": (C.c_int, [_P, C.c_char_p, _P, C.c_int, _P]),
 }
 
 _lib = None
@@ -240,9 +244,9 @@ def dpm_diag_philox(ctx, ctr, key) -> np.ndarray:
 
 
 def run_opts(kernel=KERNEL_QUEUE, n_batches=0, block_size=0, blocks_per_sm=0, queue_log2=0, refill_min=0,
-             timeout_s=0.0, physics_flags=0) -> dpm_run_opts:
+             timeout_s=0.0, physics_flags=0, queue_limit=0) -> dpm_run_opts:
     return dpm_run_opts(kernel, n_batches, block_size, blocks_per_sm, queue_log2, refill_min, timeout_s,
-                        physics_flags)
+                        physics_flags, queue_limit)
 
 
 class Dpm:
@@ -290,3 +294,36 @@ def dpm_load_phantom_raw(ctx, nx, ny, nz, dx, dy, dz, mat_ptr: int, rho_ptr: int
     pid = C.c_int(-1)
     _check(ctx, lib().dpm_load_phantom(ctx, nx, ny, nz, dx, dy, dz, _P(mat_ptr), _P(rho_ptr), C.byref(pid)))
     return pid.value
+
+
+class HostTables:
+    """The tables as the library builds them, read on the host (no GPU)."""
+
+    def __init__(self, materials, params: dict):
+        arr = (dpm_material * len(materials))(*[material_struct(m) for m in materials])
+        pp = params_struct(params)
+        err = C.create_string_buffer(256)
+        self.h = lib().dpm_host_tables_build(arr, len(materials), C.byref(pp), err)
+        if not self.h:
+            raise DpmError(DPM_EINVAL, err.value.decode())
+
+    def get(self, name: str):
+        meta = (C.c_double * 6)()
+        n = lib().dpm_host_tables_get(self.h, name.encode(), None, 0, meta)
+        if n < 0:
+            raise KeyError(name)
+        a = np.zeros(n, np.float32)
+        lib().dpm_host_tables_get(self.h, name.encode(), _ptr(a), n, meta)
+        return a, list(meta)
+
+    def close(self):
+        if self.h:
+            lib().dpm_host_tables_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -13,9 +13,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    text = open(os.path.join(ROOT, "include", "dpm.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(dpm_[a-z_0-9]+)\s*\(", text)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            text = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(dpm_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary_calls():
@@ -47,4 +51,4 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(dpm.dpm_material) == 4 + 4 + 3 * 8 * 8 + 8
     assert ctypes.sizeof(dpm.dpm_table_params) == 7 * 8 + 8
     assert ctypes.sizeof(dpm.dpm_source) == 8 + 8 + 3 * 8 + 4 * 8
-    assert ctypes.sizeof(dpm.dpm_run_opts) == 6 * 4 + 8 + 8
+    assert ctypes.sizeof(dpm.dpm_run_opts) == 6 * 4 + 8 + 2 * 4

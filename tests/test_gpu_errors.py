@@ -58,7 +58,7 @@ def test_queue_overflow_is_reported_and_recoverable():
     wl = W.c1_photon_wbw()
     with dpm.Dpm(0, W.MATERIALS, wl.params) as d:
         pid = d.load_phantom(wl.phantom)
-        d.run(pid, wl.source, 400000, wl.seed, kernel=dpm.KERNEL_QUEUE, queue_log2=7, refill_min=1)
+        d.run(pid, wl.source, 400000, wl.seed, kernel=dpm.KERNEL_QUEUE, queue_limit=1)
         with pytest.raises(dpm.DpmError) as e:
             d.read(pid)
         assert e.value.code == dpm.DPM_EQUEUE_OVERFLOW

@@ -14,10 +14,13 @@ pytestmark = pytest.mark.gpu
 P = W.DEFAULT_PARAMS
 MC2 = 0.51099895
 U = np.linspace(0.0005, 0.9995, 160)
-# bilinear interpolation on a 256 x 129 grid of a smooth normalised inverse
-# CDF: error ~ (1/128)^2/8 * y'' in u plus (dlnE)^2/8 * y'' in energy; 2e-3 in
-# probability bounds both for these densities.
-TOL = 2e-3
+# Bilinear interpolation on a 256 x 129 grid of a normalised inverse CDF has
+# error ~ (1/128)^2/8 * y'' in u plus (dlnE)^2/8 * y'' in energy.  The bounds
+# below are about twice the largest error of the host-built tables (measured
+# on the CPU, tests/test_host_tables.py): KN 2e-5, brems 3e-5, Moller 3e-4
+# (rows at 20 MeV), pair 2e-3 (the density vanishes at the ends of its
+# support, so the inverse CDF is steep there), MSC 2e-6.
+TOL = {"kn": 1e-4, "mol": 6e-4, "brem": 1e-4, "pair": 4e-3, "msc": 1e-5}
 
 
 def quad(f, a, b):
@@ -29,7 +32,7 @@ def test_kn(tables_ctx, E):
     L = O.lib()
     x = dpm.dpm_diag_sample(tables_ctx.ctx, 0, E, 0.0, U)
     F = np.array([L.or_kn_cdf(E, e) for e in x])
-    assert np.max(np.abs(F - U)) < TOL
+    assert np.max(np.abs(F - U)) < TOL["kn"]
 
 
 @pytest.mark.parametrize("T", [0.45, 1.0, 5.0, 20.0])
@@ -39,7 +42,7 @@ def test_moller(tables_ctx, T):
     x = dpm.dpm_diag_sample(tables_ctx.ctx, 1, T, 0.0, U)
     tot = L.or_moller_sigma(m, T, wcc)
     F = np.array([quad(lambda w: L.or_moller_dsdw(m, T, w), wcc, e * T) / tot for e in x])
-    assert np.max(np.abs(F - U)) < TOL
+    assert np.max(np.abs(F - U)) < TOL["mol"]
 
 
 @pytest.mark.parametrize("T", [0.1, 0.6, 5.0, 20.0])
@@ -49,7 +52,7 @@ def test_brems(tables_ctx, T):
     x = dpm.dpm_diag_sample(tables_ctx.ctx, 2, T, 0.0, U)
     tot = L.or_brems_sigma(m, T, wcr)
     F = np.array([quad(lambda k: L.or_brems_dsdk(m, T, k), wcr, k) / tot for k in x])
-    assert np.max(np.abs(F - U)) < TOL
+    assert np.max(np.abs(F - U)) < TOL["brem"]
 
 
 @pytest.mark.parametrize("E", [1.9, 3.0, 6.0, 20.0])
@@ -62,7 +65,7 @@ def test_pair(tables_ctx, E):
     f = lambda e: L.or_pair_dsde_shape(k, e, 1)
     tot = quad(f, lo, hi)
     F = np.array([quad(f, lo, e) / tot for e in x])
-    assert np.max(np.abs(F - U)) < TOL
+    assert np.max(np.abs(F - U)) < TOL["pair"]
 
 
 @pytest.mark.parametrize("q", [1e-6, 1e-3, 0.05, 0.4, 0.9, 0.999])
@@ -71,7 +74,7 @@ def test_msc(tables_ctx, q):
     A = L.or_msc_A(q)
     x = dpm.dpm_diag_sample(tables_ctx.ctx, 4, 1.0, q, U)
     F = (1 + A) * x / (x + 2 * A)
-    assert np.max(np.abs(F - U)) < TOL
+    assert np.max(np.abs(F - U)) < TOL["msc"]
 
 
 def test_spectrum(tables_ctx):
