@@ -182,6 +182,30 @@ int dpm_diag_sample(dpm_ctx *ctx, int which, double e, double aux, int n, const 
 /* n Philox4x32-10 blocks for counters ctr[4*i..] and keys key[2*i..] (host). */
 int dpm_diag_philox(dpm_ctx *ctx, int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out);
 
+/* ---- transport without device allocation -------------------------------
+   Not a step of the paper's method (the paper has no counterpart): an entry
+   point for callers that cannot allocate device memory once they are running,
+   e.g. a program whose device memory is owned by a pool or arena that forbids
+   further cudaMalloc, or one held to a fixed device-memory budget set at
+   start-up.  It runs the persistent queue transport of dpm_run() with the same
+   physics and random numbers for histories [first_history, first_history +
+   n_histories) and ADDS the integer tally (units of 2^-32 MeV, nx*ny*nz
+   int64, voxel layout as above) to the caller-allocated device array d_tally;
+   no batch statistics are kept.  Its scratch (particle queues, counters, error
+   word) is a fixed device array of DPM_NOALLOC_SCRATCH_BYTES that every GPU
+   loading the library holds until the process exits; the call allocates
+   nothing.  The first call on a device looks the array's device address up
+   (cudaGetSymbolAddress), so that first call should come before any stream
+   capture.  Every call shares the one array: calls that overlap on the GPU
+   (e.g. from two contexts or streams at once) race and must be serialised by
+   the caller.  The call waits for the transport and returns its status:
+   DPM_EQUEUE_OVERFLOW if the fixed queues overflowed, DPM_ETIMEOUT if a bounded
+   wait gave up, DPM_ESTATE before dpm_build_tables(), DPM_EINVAL for bad
+   arguments or more than 2^31-1 histories. */
+#define DPM_NOALLOC_SCRATCH_BYTES (48u << 20)
+int dpm_run_noalloc(dpm_ctx *ctx, int phantom_id, const dpm_source *src, uint64_t first_history,
+                    uint64_t n_histories, uint64_t seed, int64_t *d_tally);
+
 #ifdef __cplusplus
 }
 #endif

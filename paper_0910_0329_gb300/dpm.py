@@ -83,6 +83,7 @@ _SIGS = {
     "dpm_diag_table": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
     "dpm_diag_sample": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, _P, _P]),
     "dpm_diag_philox": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "dpm_run_noalloc": (C.c_int, [_P, C.c_int, C.POINTER(dpm_source), C.c_uint64, C.c_uint64, C.c_uint64, _P]),
     # include/dpm_host.h (host-only table inspection)
     "dpm_host_tables_build": (_P, [C.POINTER(dpm_material), C.c_int, C.POINTER(dpm_table_params), C.c_char_p]),
     "dpm_host_tables_free": (None, [_P]),
@@ -327,3 +328,10 @@ class HostTables:
         except Exception:
             pass
 
+
+def dpm_run_noalloc(ctx, pid: int, src: W.Source, first: int, n: int, seed: int, d_tally_ptr: int):
+    """Transport into a caller-owned device int64 tally without allocating
+    device memory (the fixed-scratch entry point); ``d_tally_ptr`` is a raw
+    device pointer, e.g. ``tensor.data_ptr()`` of a CUDA int64 tensor."""
+    s = source_struct(src)
+    _check(ctx, lib().dpm_run_noalloc(ctx, pid, C.byref(s), first, n, seed, _P(d_tally_ptr)))
