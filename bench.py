@@ -42,6 +42,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU work of the oracle baseline sample")
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="history scale of the batch64 workload")
+    ap.add_argument("--autotune", action="store_true", help="tune the batched launch before timing it")
+    ap.add_argument("--requests", type=int, default=500, help="requests of the serve workload")
+    ap.add_argument("--rate", type=float, default=20.0, help="request arrival rate of the serve workload (1/s)")
+    ap.add_argument("--chunk", type=int, default=200000, help="histories per request and round (serve)")
     return ap.parse_args()
 
 
@@ -191,6 +196,13 @@ def main():
             tdist.destroy_process_group()
         return
 
+    if args.workload == "batch64":
+        bench_batch(args, rank, world, local)
+        return
+    if args.workload == "serve":
+        bench_serve(args, rank, world, local)
+        return
+
     import numpy as np
     import torch
 
@@ -301,6 +313,124 @@ def main():
         import torch.distributed as tdist
 
         tdist.destroy_process_group()
+
+
+def bench_batch(args, rank, world, local):
+    """64 phantoms and beams of uneven size in one persistent launch per step
+    (graph-replayed), against the plain path: the same 64 jobs as 64 dpm_run
+    calls on the same GPU."""
+    import torch
+
+    from paper_0910_0329_gb300 import autotune, build_lib, dpm, sharding
+    from paper_0910_0329_gb300 import workloads as W
+
+    build_lib.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    spec = W.c3_batch(scale=args.batch_scale)
+    params = dict(W.DEFAULT_PARAMS, e_max=21.0)
+    d = dpm.Dpm(local, W.MATERIALS, params, stream=stream)
+    pids = [d.load_phantom(ph) for ph, _, _, _ in spec]
+    n_step = sum(n for _, _, n, _ in spec)
+    opts = {}
+    if args.autotune:
+        jobs0 = [(pid, src, 0, n, seed) for pid, (ph, src, n, seed) in zip(pids, spec)]
+        opts = autotune.tune_batch(d, jobs0, torch.cuda.get_device_name(local), f"batch64x{args.batch_scale}")
+
+    def jobs_for(step):
+        out = []
+        for pid, (ph, src, n, seed) in zip(pids, spec):
+            first, _ = sharding.history_range(rank, world, step, n)
+            out.append((pid, src, first, n, seed))
+        return out
+
+    ro = dpm.run_opts(use_graph=1, n_batches=10, **opts)
+    for i in range(args.warmup):
+        dpm.dpm_run_batch(d.ctx, jobs_for(1000 + i), ro)
+    dpm.dpm_batch_stats(d.ctx)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        dpm.dpm_run_batch(d.ctx, jobs_for(i), ro)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    st = dpm.dpm_batch_stats(d.ctx)
+    batch_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    # the plain single-run path: the same jobs one dpm_run at a time
+    plain = []
+    for rep in range(2):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for pid, src, first, n, seed in jobs_for(2000 + rep):
+            dpm.dpm_run(d.ctx, pid, src, first, n, seed, dpm.run_opts(n_batches=10, **opts))
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain.append(a.elapsed_time(b))
+    plain_ms = min(plain)
+    d.close()
+    value = world * n_step / (batch_ms / 1000.0)
+    line = {"metric": "histories/s", "value": value, "unit": "histories/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch64", "jobs": len(spec), "histories_per_step": n_step,
+                       "voxels_total": int(sum(ph.n_vox for ph, *_ in spec)),
+                       "launch": "one persistent queue launch per step, CUDA-graph replay (zero -> transport -> fold)",
+                       "tuned_opts": opts, "parallelism": f"{world} replica(s)"},
+            "single_run_path": {"ms_per_step": plain_ms, "value": world * n_step / (plain_ms / 1000.0),
+                                "what": "the same 64 jobs as 64 dpm_run calls"},
+            "speedup_vs_single_runs": plain_ms / batch_ms,
+            "batch_error_flags": st["error_flags"],
+            "clocks": clk, "gpu_launches": args.steps * (2 + len(spec))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def bench_serve(args, rank, world, local):
+    """Poisson stream of 6 MV beamlet requests (0.5 x 0.5 cm, uniform gantry
+    angle) on 8 resident 128^3 blob phantoms of 0.3 cm voxels, each served to
+    1 % sigma at D_max with continuous batching; against the plain path that
+    serves one request at a time.  Replicas only under torchrun."""
+    import torch
+
+    from paper_0910_0329_gb300 import build_lib, serve
+    from paper_0910_0329_gb300 import workloads as W
+
+    build_lib.build()
+    torch.cuda.set_device(local)
+    geoms = [W.blob_phantom(128, 128, 128, 0.3, 100 + k, name=f"patient{k}") for k in range(8)]
+    ext = [g.extent for g in geoms]
+
+    def run(max_active):
+        reqs = serve.poisson_requests(args.requests, args.rate, 8, seed=5 + rank, geom_extent=ext)
+        s = serve.Server(geoms, hbm_budget=48 << 30, chunk=args.chunk, target=0.01, max_active=max_active,
+                         device=local)
+        warm = serve.poisson_requests(4, 1000.0, 8, seed=99, geom_extent=ext)
+        s.run(warm)  # allocations and first launches
+        s.stats = serve.ServeStats()
+        clocks = Clocks(local)
+        clocks.start()
+        st = s.run(reqs)
+        clk = clocks.stop()
+        s.close()
+        return st.summary(), clk
+
+    batched, clk = run(1024)
+    plain, _ = run(1)
+    line = {"metric": "histories/s", "value": batched["histories_per_s"] * world, "unit": "histories/s",
+            "n_gpus": world, "steps": args.requests, "warmup": 4, "ms_per_step": 1000 * batched["wall_s"] / args.requests,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serve", "requests": args.requests, "rate_per_s": args.rate,
+                       "geometries": "8 x 128^3 x 0.3 cm blob phantoms", "beamlet": "6 MV 0.5x0.5 cm, gantry U[0,360)",
+                       "target": "1 % sigma at D_max", "chunk": args.chunk, "parallelism": f"{world} replica(s)"},
+            "p50_latency_s": batched["p50_latency_s"], "p99_latency_s": batched["p99_latency_s"],
+            "served": batched, "single_request_path": plain, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def e2e(args, d, wl, n, kernel, local):

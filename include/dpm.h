@@ -99,6 +99,8 @@ typedef struct {
                           elastic deflections (test and ablation switches; 0 = full physics) */
     int queue_limit;   /* fault injection: largest occupancy of a queue shard (0 = capacity);
                           a push that finds no shard below it is an overflow */
+    int use_graph;     /* dpm_run_batch only: capture zero -> transport -> fold in a CUDA
+                          graph and replay it while the batch keeps its shape */
 } dpm_run_opts;
 enum { DPM_NO_HARD = 1, DPM_NO_MSC = 2 };
 
@@ -146,6 +148,29 @@ int dpm_build_tables(dpm_ctx *ctx, const dpm_material *mats, int n_mat, const dp
 int dpm_run(dpm_ctx *ctx, int phantom_id, const dpm_source *src, uint64_t first_history,
             uint64_t n_histories, uint64_t seed, const dpm_run_opts *opts);
 
+/* One entry of a batch: a loaded phantom, a beam, a history range and a seed. */
+typedef struct {
+    int phantom_id;
+    dpm_source src;
+    uint64_t first_history, n_histories, seed;
+} dpm_job;
+
+/* Transport several jobs in ONE persistent queue launch (up to 1024 jobs on
+   distinct phantoms).  New histories are drawn job after job while the
+   particles of earlier jobs are still in flight, so the GPU stays full across
+   job boundaries.  Each job accumulates into its phantom's tally exactly as
+   dpm_run() with the same arguments would: the random numbers are keyed by
+   (seed, history, particle), so the integer tally is the same.  With
+   opts->use_graph the device work (zero slabs -> transport -> folds) is
+   captured in a CUDA graph on the first call and replayed on later calls whose
+   jobs have the same phantoms, history counts and options; the history ranges,
+   seeds and beams may change between replays.  Asynchronous like dpm_run(). */
+int dpm_run_batch(dpm_ctx *ctx, const dpm_job *jobs, int n_jobs, const dpm_run_opts *opts);
+
+/* Counters (summed over jobs) and transport time of the batches run since
+   the previous call; synchronises and reports device-side errors. */
+int dpm_batch_stats(dpm_ctx *ctx, dpm_run_stats *stats);
+
 /* Zero the phantom's accumulated tally and statistics. */
 int dpm_reset_tally(dpm_ctx *ctx, int phantom_id);
 
@@ -159,6 +184,13 @@ int dpm_read_dose(dpm_ctx *ctx, int phantom_id, double *dose_gy, double *sigma_g
 /* Same, writing dose and sigma into caller-allocated *device* arrays. */
 int dpm_read_dose_device(dpm_ctx *ctx, int phantom_id, double *d_dose_gy, double *d_sigma_gy,
                          dpm_run_stats *stats);
+
+/* The stop rule of a dose request (Sec. 3 reports sigma_D/D; here at D_max):
+   for each of n phantoms, find on the device the voxel of largest accumulated
+   dose and return its dose (Gy per history), its sigma (batch method) and its
+   index in out[3*i .. 3*i+2] (index -1 when nothing was deposited).
+   Synchronises.  ids and out are host arrays. */
+int dpm_dmax_sigma(dpm_ctx *ctx, const int *phantom_ids, int n, double *out);
 
 /* Wait for queued work; reports device-side errors of earlier runs. */
 int dpm_sync(dpm_ctx *ctx);

@@ -65,6 +65,7 @@ void free_phantom(PhantomState *p) {
   cudaFree(p->d_inv_nb);
   cudaFree(p->d_dose);
   cudaFree(p->d_sigma);
+  cudaFree(p->d_dmax);
 }
 
 void free_tables(dpm_ctx *c) {
@@ -118,6 +119,29 @@ uint64_t splitmix(uint64_t x) {
 namespace dpm {
 
 int ctx_fail(dpm_ctx *c, int code, const std::string &msg) { return fail(c, code, msg); }
+
+int ctx_alloc(dpm_ctx *c, void **p, size_t bytes) { return dalloc(c, reinterpret_cast<char **>(p), bytes); }
+
+int ctx_prepare_batches(dpm_ctx *c, PhantomState *p, uint64_t n, int n_batches, uint64_t &bs, int &B) {
+  int nb = n_batches > 0 ? n_batches : 50;
+  if (nb > 1024) return fail(c, DPM_EINVAL, "n_batches must be <= 1024");
+  if (uint64_t(nb) > n) nb = int(n);
+  bs = (n + nb - 1) / nb;
+  B = int((n + bs - 1) / bs);
+  int rc;
+  if (p->slab_batches < size_t(B)) {
+    cudaFree(p->d_slabs);
+    p->d_slabs = nullptr;
+    p->slab_batches = 0;
+    if ((rc = dalloc(c, &p->d_slabs, size_t(B) * p->V))) return rc;
+    p->slab_batches = size_t(B);
+  }
+  std::vector<double> inv_nb(B);
+  for (int b = 0; b < B; ++b) inv_nb[b] = 1.0 / double(std::min<uint64_t>(bs, n - uint64_t(b) * bs));
+  CUDA_TRY(c, cudaMemcpyAsync(p->d_inv_nb, inv_nb.data(), B * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  // pageable source: the copy is staged before the call returns
+  return DPM_OK;
+}
 
 PhantomState *ctx_phantom(dpm_ctx *c, int id) { return get_phantom(c, id); }
 
@@ -203,6 +227,10 @@ void dpm_destroy(dpm_ctx *c) {
   for (auto &p : c->phantoms) free_phantom(p.get());
   free_tables(c);
   queue_free(c->queue);
+  cudaFree(c->d_jobs);
+  cudaFree(c->d_batch_counters);
+  for (cudaEvent_t e : c->batch_ev) cudaEventDestroy(e);
+  if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
   cudaFree(c->d_err);
   if (c->own) cudaStreamDestroy(c->own);
   delete c;
@@ -342,22 +370,10 @@ int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t 
   int rc = ctx_run_params(c, p, src, first, n, seed, o.physics_flags, R);
   if (rc) return rc;
   if (n == 0) return DPM_OK;
-  int nb = o.n_batches > 0 ? o.n_batches : 50;
-  if (nb > 1024) return fail(c, DPM_EINVAL, "n_batches must be <= 1024");
-  if (uint64_t(nb) > n) nb = int(n);
-  const uint64_t bs = (n + nb - 1) / nb;
-  const int B = int((n + bs - 1) / bs);
   cudaSetDevice(c->device);
-  if (p->slab_batches < size_t(B)) {
-    cudaFree(p->d_slabs);
-    p->d_slabs = nullptr;
-    p->slab_batches = 0;
-    if ((rc = dalloc(c, &p->d_slabs, size_t(B) * p->V))) return rc;
-    p->slab_batches = size_t(B);
-  }
-  std::vector<double> inv_nb(B);
-  for (int b = 0; b < B; ++b) inv_nb[b] = 1.0 / double(std::min<uint64_t>(bs, n - uint64_t(b) * bs));
-  CUDA_TRY(c, cudaMemcpyAsync(p->d_inv_nb, inv_nb.data(), B * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  uint64_t bs = 0;
+  int B = 0;
+  if ((rc = ctx_prepare_batches(c, p, n, o.n_batches, bs, B))) return rc;
   CUDA_TRY(c, cudaMemsetAsync(p->d_slabs, 0, size_t(B) * p->V * sizeof(unsigned long long), c->stream));
   R.n_batches = B;
   R.slabs = p->d_slabs;
@@ -383,6 +399,32 @@ int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t 
   p->n_total += n;
   p->b_total += uint64_t(B);
   return DPM_OK;
+}
+
+int dpm_dmax_sigma(dpm_ctx *c, const int *ids, int n, double *out) {
+  if (!c) return DPM_EINVAL;
+  if (n < 0 || (n > 0 && (!ids || !out))) return fail(c, DPM_EINVAL, "bad arguments");
+  cudaSetDevice(c->device);
+  std::vector<PhantomState *> ps(n);
+  for (int i = 0; i < n; ++i) {
+    ps[i] = get_phantom(c, ids[i]);
+    if (!ps[i]) return fail(c, DPM_EINVAL, "bad phantom id");
+    if (!ps[i]->d_dmax) {
+      int rc = dalloc(c, &ps[i]->d_dmax, size_t(4));
+      if (rc) return rc;
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    PhantomState *p = ps[i];
+    launch_dmax(p->d_S1, p->d_Q, p->d_rho, p->V, double(p->n_total), double(p->b_total), p->dx * p->dy * p->dz,
+                p->d_dmax, reinterpret_cast<double *>(p->d_dmax + 1), c->sm_count, c->stream);
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  const int src = dpm_sync(c);
+  if (src == DPM_ECUDA) return src;
+  for (int i = 0; i < n; ++i)
+    CUDA_TRY(c, cudaMemcpy(out + 3 * i, ps[i]->d_dmax + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost));
+  return src;
 }
 
 int dpm_sync(dpm_ctx *c) {

@@ -32,6 +32,7 @@ struct PhantomState {
   unsigned long long *d_counters = nullptr;
   double *d_inv_nb = nullptr;
   double *d_dose = nullptr, *d_sigma = nullptr;
+  unsigned long long *d_dmax = nullptr;  // [1] key + [3] doubles for the D_max query
   uint64_t n_total = 0;
   uint64_t b_total = 0;
   // CUDA events around each transport launch and fold since the last read
@@ -54,6 +55,13 @@ struct dpm_ctx {
   std::vector<std::unique_ptr<dpm::PhantomState>> phantoms;
   int *d_err = nullptr;
   dpm::QueueState queue;
+  // batches
+  dpm::DevJob *d_jobs = nullptr;               // job table, kMaxJobs entries
+  unsigned long long *d_batch_counters = nullptr;  // [C_N]
+  std::vector<cudaEvent_t> batch_ev;           // start/end pairs since the last dpm_batch_stats
+  uint64_t batch_histories = 0;
+  cudaGraphExec_t batch_exec = nullptr;
+  std::vector<uint64_t> batch_sig;             // shape the cached graph was captured for
 };
 
 namespace dpm {
@@ -64,5 +72,10 @@ PhantomState *ctx_phantom(dpm_ctx *c, int id);
 // batch size are left to the caller).  Allocates nothing.
 int ctx_run_params(dpm_ctx *c, PhantomState *p, const dpm_source *src, uint64_t first, uint64_t n, uint64_t seed,
                    int physics_flags, RunParams &R);
+// Device allocation owned by the context (error message set on failure).
+int ctx_alloc(dpm_ctx *c, void **p, size_t bytes);
+// Batch structure of a run of n histories in (at most) n_batches batches:
+// makes sure the phantom has B slabs and uploads 1/n_b; returns bs and B.
+int ctx_prepare_batches(dpm_ctx *c, PhantomState *p, uint64_t n, int n_batches, uint64_t &bs, int &B);
 
 }  // namespace dpm

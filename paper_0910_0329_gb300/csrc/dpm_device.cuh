@@ -2,6 +2,11 @@
 // transport kernels.  Every function follows the DPM scheme of Sec. 2.1 with
 // the closed-form model tabulated by dpm_tables.cpp.
 //
+// A "context" C supplies what a particle's history needs: C.T (tables), C.P
+// (phantom), C.S (source), C.first, C.key0, C.key1 (history numbering and
+// Philox key).  RunParams (one run) and JobCtx (one entry of a batch) both
+// provide these members.
+//
 // A "sink" object receives what the physics produces:
 //   sink.deposit(v, dE)  energy dE (MeV) deposited in voxel v
 //   sink.escape(E)       energy carried out of the phantom
@@ -64,18 +69,30 @@ struct Part {
   int ix, iy, iz;
   uint32_t id_lo, id_hi;  // particle id within its history
   uint32_t ctr;           // next Philox block of this particle
-  uint32_t hist;          // history index relative to the run
+  uint32_t hist;          // history index relative to the run (or job)
   int type;
+  int job;                // index in the batch's job table (0 for a single run)
 };
 
 // Philox key of a history: seed hash xor the global history id; the third
 // counter word carries more seed bits so that different seeds never share
 // streams.
-__device__ __forceinline__ uint4 draw(Part &p, const RunParams &R) {
+template <class Ctx>
+__device__ __forceinline__ uint4 draw(Part &p, const Ctx &R) {
   const uint64_t h = R.first + p.hist;
   const uint4 c = make_uint4(p.ctr++, p.id_lo, p.id_hi, R.key0 ^ 0x5bd1e995u);
   return philox4x32_10(c, R.key0 ^ uint32_t(h), R.key1 ^ uint32_t(h >> 32));
 }
+
+// Context of one batch job: references into the job table (global memory)
+// plus the history numbering held in registers.
+struct JobCtx {
+  const DevTables &T;
+  const DevPhantom &P;
+  const DevSource &S;
+  uint64_t first;
+  uint32_t key0, key1;
+};
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -265,8 +282,8 @@ __device__ __forceinline__ float spectrum_6mv(float u) {
 // Emission helpers: below the absorption energy a new particle deposits on the
 // spot (Sec. 3); a positron then also annihilates.
 // ---------------------------------------------------------------------------
-template <class Sink>
-__device__ DPM_COLD void annihilate(Part &p, const RunParams &R, Sink &s) {
+template <class Ctx, class Sink>
+__device__ DPM_COLD void annihilate(Part &p, const Ctx &R, Sink &s) {
   const uint4 r = draw(p, R);
   const float cz = 2.f * u01(r.x) - 1.f;
   const float sz = sqrtf(fmaxf(0.f, 1.f - cz * cz));
@@ -286,8 +303,8 @@ __device__ DPM_COLD void annihilate(Part &p, const RunParams &R, Sink &s) {
   s.push(h);
 }
 
-template <class Sink>
-__device__ void emit_charged(Part &q, const RunParams &R, Sink &s) {
+template <class Ctx, class Sink>
+__device__ void emit_charged(Part &q, const Ctx &R, Sink &s) {
   if (q.E > R.T.eabs_e) {
     s.push(q);
     return;
@@ -296,14 +313,14 @@ __device__ void emit_charged(Part &q, const RunParams &R, Sink &s) {
   if (q.type == POSITRON) annihilate(q, R, s);
 }
 
-template <class Sink>
-__device__ void emit_photon(Part &q, const RunParams &R, Sink &s) {
+template <class Ctx, class Sink>
+__device__ void emit_photon(Part &q, const Ctx &R, Sink &s) {
   if (q.E > R.T.eabs_g) s.push(q);
   else s.deposit(vox(q, R.P), q.E);
 }
 
-template <class Sink>
-__device__ void absorb_charged(Part &p, const RunParams &R, Sink &s) {
+template <class Ctx, class Sink>
+__device__ void absorb_charged(Part &p, const Ctx &R, Sink &s) {
   s.deposit(vox(p, R.P), p.E);
   if (p.type == POSITRON) annihilate(p, R, s);
 }
@@ -313,10 +330,12 @@ __device__ void absorb_charged(Part &p, const RunParams &R, Sink &s) {
 // field rectangle in the isocentre plane, flown to the phantom surface.
 // Returns false if the ray misses the phantom.
 // ---------------------------------------------------------------------------
-static __device__ DPM_COLD bool make_primary(Part &p, const RunParams &R, uint32_t hl) {
+template <class Ctx>
+__device__ DPM_COLD bool make_primary(Part &p, const Ctx &R, uint32_t hl) {
   const DevSource &S = R.S;
   const DevPhantom &P = R.P;
   p.hist = hl;
+  p.job = 0;
   p.id_lo = 1u;
   p.id_hi = 0u;
   p.ctr = 0;
@@ -362,8 +381,8 @@ static __device__ DPM_COLD bool make_primary(Part &p, const RunParams &R, uint32
 // Photons (Sec. 2.1): Woodcock flights over the majorant, then an interaction.
 // Returns true while the photon is alive (after a Compton scatter).
 // ---------------------------------------------------------------------------
-template <class Sink>
-__device__ DPM_COLD bool photon_interact(Part &p, const RunParams &R, Sink &s, EIdx e, int m) {
+template <class Ctx, class Sink>
+__device__ DPM_COLD bool photon_interact(Part &p, const Ctx &R, Sink &s, EIdx e, int m) {
   const DevTables &T = R.T;
   const uint4 r = draw(p, R);
   const float4 c = ph_at(T, m, e);
@@ -418,8 +437,8 @@ __device__ DPM_COLD bool photon_interact(Part &p, const RunParams &R, Sink &s, E
   return true;
 }
 
-template <class Sink>
-__device__ bool photon_segment(Part &p, const RunParams &R, Sink &s) {
+template <class Ctx, class Sink>
+__device__ bool photon_segment(Part &p, const Ctx &R, Sink &s) {
   const DevTables &T = R.T;
   const DevPhantom &P = R.P;
   if (p.E <= T.eabs_g) {
@@ -460,8 +479,8 @@ __device__ bool photon_segment(Part &p, const RunParams &R, Sink &s) {
 // Electrons and positrons (Sec. 2.1): one condensed-history step.
 // Returns true while the particle is alive.
 // ---------------------------------------------------------------------------
-template <class Sink>
-__device__ DPM_COLD void electron_hard(Part &p, const RunParams &R, Sink &s, float sig0, int m) {
+template <class Ctx, class Sink>
+__device__ DPM_COLD void electron_hard(Part &p, const Ctx &R, Sink &s, float sig0, int m) {
   const DevTables &T = R.T;
   const uint4 r = draw(p, R);
   const float Tn = p.E;
@@ -496,8 +515,8 @@ __device__ DPM_COLD void electron_hard(Part &p, const RunParams &R, Sink &s, flo
   }
 }
 
-template <class Sink>
-__device__ bool electron_step(Part &p, const RunParams &R, Sink &s) {
+template <class Ctx, class Sink>
+__device__ bool electron_step(Part &p, const Ctx &R, Sink &s) {
   const DevTables &T = R.T;
   const DevPhantom &P = R.P;
   if (p.E <= T.eabs_e) {

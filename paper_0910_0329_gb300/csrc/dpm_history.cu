@@ -178,4 +178,50 @@ void launch_normalize(const long long *S1, const double *Q, const float *rho, si
   k_normalize<<<grid > 0 ? grid : 1, 256, 0, st>>>(S1, Q, rho, V, n, B, vox_cm3, dose, sigma);
 }
 
+// D_max search for the stop rule: a 64-bit key (dose as float bits, which
+// order like the values for non-negative doses, above the voxel index) reduced
+// with atomicMax; then one thread evaluates dose and sigma at the winner.
+__global__ void k_dmax_key(const long long *S1, const float *rho, size_t V, double vox_cm3,
+                           unsigned long long *key) {
+  unsigned long long best = 0;
+  for (size_t v = size_t(blockIdx.x) * blockDim.x + threadIdx.x; v < V; v += size_t(gridDim.x) * blockDim.x) {
+    const double s1 = double(S1[v]);
+    if (s1 <= 0) continue;
+    const float dose = float(s1 * kMeVtoJ / (double(rho[v]) * vox_cm3 * 1e-3));
+    const unsigned long long k = (uint64_t(__float_as_uint(dose)) << 32) | uint64_t(uint32_t(v));
+    best = k > best ? k : best;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_down_sync(0xffffffffu, best, o);
+    best = other > best ? other : best;
+  }
+  if ((threadIdx.x & 31) == 0 && best) atomicMax(key, best);
+}
+
+__global__ void k_dmax_eval(const long long *S1, const double *Q, const float *rho, double n, double B,
+                            double vox_cm3, const unsigned long long *key, double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  out[0] = out[1] = 0.0;
+  out[2] = -1.0;
+  if (*key == 0 || n <= 0) return;
+  const size_t v = size_t(uint32_t(*key));
+  const double s1 = double(S1[v]);
+  const double conv = kMeVtoJ / (double(rho[v]) * vox_cm3 * 1e-3) / kTallyScale;
+  const double var = B > 1.0 ? fmax(Q[v] - s1 * s1 / n, 0.0) / (B - 1.0) : 0.0;
+  out[0] = s1 / n * conv;
+  out[1] = sqrt(var / n) * conv;
+  out[2] = double(v);
+}
+
+void launch_dmax(const long long *S1, const double *Q, const float *rho, size_t V, double n, double B, double vox_cm3,
+                 unsigned long long *key, double *out, int sm_count, cudaStream_t st) {
+  cudaMemsetAsync(key, 0, sizeof(unsigned long long), st);
+  const size_t need = (V + 255) / 256;
+  const size_t cap = size_t(sm_count) * 8;
+  const int grid = int(need < cap ? need : cap);
+  k_dmax_key<<<grid > 0 ? grid : 1, 256, 0, st>>>(S1, rho, V, vox_cm3, key);
+  k_dmax_eval<<<1, 32, 0, st>>>(S1, Q, rho, n, B, vox_cm3, key, out);
+}
+
 }  // namespace dpm

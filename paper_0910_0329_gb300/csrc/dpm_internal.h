@@ -69,6 +69,20 @@ enum {
 
 enum { ERR_OVERFLOW = 1, ERR_STEPCAP = 2, ERR_TIMEOUT = 4 };
 
+constexpr int kMaxJobs = 1024;  // entries of a batch's job table
+
+// One entry of a batch (dpm_run_batch): a phantom, a beam and a history range,
+// with the tally slabs and batch size of that phantom's run.
+struct DevJob {
+  DevPhantom P;
+  DevSource S;
+  uint64_t first, n;
+  uint32_t key0, key1;
+  unsigned long long *slabs;  // [n_batches][V]
+  uint64_t batch_size;
+  uint64_t V;
+};
+
 struct RunParams {
   DevTables T;
   DevPhantom P;
@@ -79,6 +93,9 @@ struct RunParams {
   unsigned long long *slabs;  // [n_batches][V]
   unsigned long long *counters;  // [C_N] (energies as two's-complement int64)
   int *err;
+  const DevJob *jobs;  // batch launches only: the job table (global memory)
+  int n_jobs;
+  int n_photon_jobs;   // the table lists photon-beam jobs first, then electron-beam jobs
 };
 
 // Host-built tables (FP64 closed forms evaluated, stored as FP32).

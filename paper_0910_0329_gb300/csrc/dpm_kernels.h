@@ -13,6 +13,10 @@ void launch_fold(const unsigned long long *slabs, int nb, size_t V, const double
 void launch_normalize(const long long *S1, const double *Q, const float *rho, size_t V, double n, double B,
                       double vox_cm3, double *dose, double *sigma, int sm_count, cudaStream_t st);
 
+// D_max of the accumulated tally and its sigma: out = {dose Gy/history, sigma, voxel}.
+void launch_dmax(const long long *S1, const double *Q, const float *rho, size_t V, double n, double B, double vox_cm3,
+                 unsigned long long *key, double *out, int sm_count, cudaStream_t st);
+
 void launch_diag_table(const DevTables &T, const DevPhantom &P, int which, int mat, int n, const double *E,
                        const double *aux, double *out, cudaStream_t st);
 void launch_diag_sample(const DevTables &T, int which, double e, double aux, int n, const double *u, double *out,

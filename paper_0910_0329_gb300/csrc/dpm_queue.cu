@@ -29,7 +29,36 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kQBlock = 128;
-constexpr int kStealProbes = 8;
+#ifndef DPM_STEAL_PROBES
+#define DPM_STEAL_PROBES 8
+#endif
+// The whole grid alternates between a source phase (histories start, warps
+// track particles of the beam's type) and a secondary phase (no history
+// starts, warps track the queued particles of the other type).  The
+// secondary phase starts when the other type's particles queued in all
+// shards exceed K * (capacity >> HIGH) and ends when they fall below
+// K * (capacity >> LOW); photon beams queue electrons, electron beams queue
+// bremsstrahlung and annihilation photons.  A CTA whose own shards hold more
+// than capacity >> GUARD particles starts no history.
+#ifndef DPM_PHASE_HIGH_SHIFT_G
+#define DPM_PHASE_HIGH_SHIFT_G 2
+#endif
+#ifndef DPM_PHASE_LOW_SHIFT_G
+#define DPM_PHASE_LOW_SHIFT_G 5
+#endif
+#ifndef DPM_PHASE_GUARD_SHIFT_G
+#define DPM_PHASE_GUARD_SHIFT_G 1
+#endif
+#ifndef DPM_PHASE_HIGH_SHIFT_E
+#define DPM_PHASE_HIGH_SHIFT_E 4
+#endif
+#ifndef DPM_PHASE_LOW_SHIFT_E
+#define DPM_PHASE_LOW_SHIFT_E 7
+#endif
+#ifndef DPM_PHASE_GUARD_SHIFT_E
+#define DPM_PHASE_GUARD_SHIFT_E 2
+#endif
+constexpr int kStealProbes = DPM_STEAL_PROBES;
 constexpr int kSpillProbes = 8;
 
 struct alignas(128) Ctl {
@@ -39,7 +68,7 @@ struct alignas(128) Ctl {
 
 struct QType {
   float *x, *y, *z, *u, *v, *w, *E;
-  uint32_t *vox, *idl, *idh, *hist, *seq;
+  uint32_t *vox, *idl, *idh, *hist, *job, *seq;
   Ctl *head, *tail;  // [K]
 };
 
@@ -48,8 +77,14 @@ struct QDev {
   int K, log2cs;
   uint32_t mask;
   Ctl *next_hist, *idle, *started;
+  Ctl *backlog;   // queued particles of each type, all shards (signed; pushes add, claims subtract) [2]
+  Ctl *phase;     // 0 source phase, 1 secondary phase
+  Ctl *cur_job;   // batch launches: per beam type (photon, electron), the first job
+                  // of that type that may still have histories to start [2]
+  Ctl *job_next;  // batch launches: next history of each job [kMaxJobs]
   int refill_min;
-  uint32_t high_water;
+  uint32_t guard[2];               // per-shard bound for sources, by beam type
+  long long phase_high[2], phase_low[2];  // global backlog thresholds, by beam type
   uint32_t limit;  // pushes beyond this occupancy of a shard spill over (fault injection can lower it)
   unsigned long long timeout_ns;   // bound on any single wait
   unsigned long long deadline_ns;  // bound on the whole launch (from kernel start)
@@ -151,6 +186,7 @@ struct QSink {
         const unsigned long long tl = ld_volatile(&Qt.tail[s].v);
         if (occupancy(h, tl) + __popc(mask) <= Q.limit) {
           base = atomicAdd(&Qt.tail[s].v, (unsigned long long)__popc(mask));
+          atomicAdd(&Q.backlog[t].v, (unsigned long long)__popc(mask));
           shard = s;
           break;
         }
@@ -188,6 +224,7 @@ struct QSink {
     Qt.idl[idx] = q.id_lo;
     Qt.idh[idx] = q.id_hi;
     Qt.hist[idx] = q.hist | (q.type == POSITRON ? 0x80000000u : 0u);
+    Qt.job[idx] = uint32_t(q.job);
     __threadfence();
     *(volatile uint32_t *)(Qt.seq + idx) = uint32_t(p + 1);
   }
@@ -249,6 +286,7 @@ __device__ __forceinline__ bool take(const QDev &Q, int t, int s, unsigned long 
   const uint32_t h = __ldcg(Qt.hist + idx);
   o.hist = h & 0x7fffffffu;
   o.type = t == 0 ? PHOTON : ((h >> 31) ? POSITRON : ELECTRON);
+  o.job = int(__ldcg(Qt.job + idx));
   o.ctr = 0;
   __threadfence();
   *(volatile uint32_t *)(Qt.seq + idx) = uint32_t(p + (1ull << Q.log2cs));
@@ -270,6 +308,7 @@ __device__ int refill_queue(const QDev &Q, int t, int home, int probes, unsigned
     n = claim(Q.q[t], s, want, base);
   }
   if (n == 0) return 0;
+  if (lane == 0) atomicAdd(&Q.backlog[t].v, (unsigned long long)(-(long long)n));
   if (empty & (1u << lane)) {
     const int rank = __popc(empty & lanemask_lt());
     if (rank < n) alive = take(Q, t, s, base + rank, p, err);
@@ -277,45 +316,132 @@ __device__ int refill_queue(const QDev &Q, int t, int home, int probes, unsigned
   return n;
 }
 
-// Start new source histories in the empty lanes.
-__device__ int refill_source(const RunParams &R, const QDev &Q, unsigned empty, Part &p, bool &alive, QSink &sk) {
+// Context of a batch job for the physics (the job table lives in global memory).
+__device__ __forceinline__ JobCtx job_ctx(const RunParams &R, int j) {
+  const DevJob &J = R.jobs[j];
+  return JobCtx{R.T, J.P, J.S, J.first, J.key0, J.key1};
+}
+
+// Start new source histories in the empty lanes: from the run's range, or
+// (batch) from the current job of the batch, job after job, so that one
+// job's phantom and tally are hot in L2 at a time.  A warp holding particles
+// of one type only starts histories of a job with that beam type (type < 0:
+// any job; the warp then takes the job's type).
+template <bool kMulti>
+__device__ int refill_source(const RunParams &R, const QDev &Q, unsigned empty, Part &p, bool &alive, QSink &sk,
+                             int &type) {
   const int want = __popc(empty);
   if (want == 0) return 0;
   const int lane = threadIdx.x & 31;
-  unsigned long long b = R.n;
-  if (lane == 0 && ld_volatile(&Q.next_hist->v) < R.n) b = atomicAdd(&Q.next_hist->v, (unsigned long long)want);
+  unsigned long long b = ~0ull, n = 0;
+  int j = 0, jt = type;
+  if (lane == 0) {
+    if (!kMulti) {
+      n = R.n;
+      if (ld_volatile(&Q.next_hist->v) < R.n) b = atomicAdd(&Q.next_hist->v, (unsigned long long)want);
+    } else {
+      for (int tries = 0; tries <= R.n_jobs; ++tries) {
+        j = int(ld_volatile(&Q.cur_job[0].v));
+        if (j >= R.n_jobs) break;
+        jt = R.jobs[j].S.particle == 0 ? 0 : 1;
+        if (type >= 0 && jt != type) break;  // the current job has the other beam type
+        n = R.jobs[j].n;
+        if (ld_volatile(&Q.job_next[j].v) < n) {
+          b = atomicAdd(&Q.job_next[j].v, (unsigned long long)want);
+          if (b < n) break;
+        }
+        atomicCAS(&Q.cur_job[0].v, (unsigned long long)j, (unsigned long long)(j + 1));  // job exhausted
+        b = ~0ull;
+      }
+    }
+  }
   b = __shfl_sync(kFull, b, 0);
-  if (b >= R.n) return 0;
+  n = __shfl_sync(kFull, n, 0);
+  j = __shfl_sync(kFull, j, 0);
+  jt = __shfl_sync(kFull, jt, 0);
+  if (b >= n) return 0;
+  type = jt;
   if (empty & (1u << lane)) {
     const unsigned long long hl = b + __popc(empty & lanemask_lt());
-    if (hl < R.n) {
-      const bool hit = make_primary(p, R, uint32_t(hl));
+    if (hl < n) {
+      bool hit;
+      if (kMulti) {
+        hit = make_primary(p, job_ctx(R, j), uint32_t(hl));
+        p.job = j;
+      } else {
+        hit = make_primary(p, R, uint32_t(hl));
+      }
       sk.cnt[C_EMIT] += QSink::fx(p.E);
       if (!hit) sk.cnt[C_MISS] += QSink::fx(p.E);
       alive = hit;
     }
   }
-  return int(min((unsigned long long)want, R.n - b));
+  return int(min((unsigned long long)want, n - b));
 }
 
 // Any queued particle anywhere, or histories left to start (warp-uniform).
+template <bool kMulti>
 __device__ bool any_work(const RunParams &R, const QDev &Q) {
   bool w = false;
   for (int s = threadIdx.x & 31; s < Q.K && !w; s += 32)
     for (int t = 0; t < 2; ++t)
       if (occupancy(ld_volatile(&Q.q[t].head[s].v), ld_volatile(&Q.q[t].tail[s].v)) > 0) w = true;
-  if ((threadIdx.x & 31) == 0 && ld_volatile(&Q.next_hist->v) < R.n) w = true;
+  if ((threadIdx.x & 31) == 0) {
+    if (!kMulti && ld_volatile(&Q.next_hist->v) < R.n) w = true;
+    if (kMulti && ld_volatile(&Q.cur_job[0].v) < (unsigned long long)R.n_jobs) w = true;
+  }
   return __any_sync(kFull, w);
 }
 
 // False while either of the CTA's shards is above its high-water mark.
-__device__ bool source_allowed(const RunParams &R, const QDev &Q, int home) {
+// True while both of the CTA's shards hold at most `bound` particles (warp-uniform).
+__device__ bool source_allowed(const QDev &Q, int home, unsigned long long bound) {
   bool ok = true;
   if ((threadIdx.x & 31) == 0) {
     for (int t = 0; t < 2; ++t)
-      if (occupancy(ld_volatile(&Q.q[t].head[home].v), ld_volatile(&Q.q[t].tail[home].v)) > Q.high_water) ok = false;
+      if (occupancy(ld_volatile(&Q.q[t].head[home].v), ld_volatile(&Q.q[t].tail[home].v)) > bound) ok = false;
   }
   return __shfl_sync(kFull, ok, 0);
+}
+
+// The grid-wide phase (0 source, 1 secondary) for beam type S, switched
+// with hysteresis on the global backlog of the other type by whichever warp
+// sees the threshold crossed first (warp-uniform).
+__device__ int grid_phase(const QDev &Q, int S) {
+  int ph = 0;
+  if ((threadIdx.x & 31) == 0) {
+    ph = int(ld_volatile(&Q.phase->v));
+    const long long b = (long long)ld_volatile(&Q.backlog[1 - S].v);
+    if (ph == 0 && b > Q.phase_high[S]) {
+      ph = 1;
+      *(volatile unsigned long long *)&Q.phase->v = 1ull;
+    } else if (ph == 1 && b < Q.phase_low[S]) {
+      ph = 0;
+      *(volatile unsigned long long *)&Q.phase->v = 0ull;
+    }
+  }
+  return __shfl_sync(kFull, ph, 0);
+}
+
+// Beam type of the batch job being started (the table lists photon beams
+// first); once every job has been started, that of the last job
+// (warp-uniform).
+__device__ __forceinline__ int current_source_type(const RunParams &R, const QDev &Q) {
+  int t = 0;
+  if ((threadIdx.x & 31) == 0) {
+    const unsigned long long j = ld_volatile(&Q.cur_job[0].v);
+    t = (j < (unsigned long long)R.n_photon_jobs || R.n_photon_jobs == R.n_jobs) ? 0 : 1;
+  }
+  return __shfl_sync(kFull, t, 0);
+}
+
+// True once every source history of the launch has been started (warp-uniform).
+template <bool kMulti>
+__device__ __forceinline__ bool source_exhausted(const RunParams &R, const QDev &Q) {
+  bool e = false;
+  if ((threadIdx.x & 31) == 0)
+    e = kMulti ? ld_volatile(&Q.cur_job[0].v) >= (unsigned long long)R.n_jobs : ld_volatile(&Q.next_hist->v) >= R.n;
+  return __shfl_sync(kFull, e, 0);
 }
 
 __device__ void reduce_counters_q(const long long *cnt, int err, const RunParams &R) {
@@ -337,7 +463,9 @@ __device__ void reduce_counters_q(const long long *cnt, int err, const RunParams
 #ifndef DPM_QUEUE_MIN_BLOCKS
 #define DPM_QUEUE_MIN_BLOCKS 8
 #endif
-__global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS) k_queue(const __grid_constant__ RunParams R, const __grid_constant__ QDev Q) {
+template <bool kMulti>
+__global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
+    k_queue(const __grid_constant__ RunParams R, const __grid_constant__ QDev Q) {
   const int lane = threadIdx.x & 31;
   const int home = blockIdx.x % Q.K;
   const int src_type = (R.S.particle == 0) ? 0 : 1;
@@ -358,24 +486,43 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS) k_queue(const _
     if (32 - __popc(live) >= Q.refill_min || live == 0) {
       const unsigned empty = ~live;
       const bool was_alive = alive;
+      const int S = kMulti ? current_source_type(R, Q) : src_type;
+      // Source phase: warps start histories and track particles of the
+      // beam's type while the secondaries of the other type pile up in
+      // the queues; secondary phase: no history starts and warps track the
+      // queued particles in full warps.  Warps of the type out of phase
+      // finish their lanes and turn over.  A grid-wide phase keeps the SMs
+      // on one of the two code paths at a time.
+      const int O = 1 - S;
+      const int ph = grid_phase(Q, S);
       if (mode < 0) {
-        // electrons first (they carry most of the work), then photons, then
-        // new histories; other shards are searched only when all that fails
-        if (refill_queue(Q, 1, home, 0, empty, p, alive, sk.err)) mode = 1;
-        else if (refill_queue(Q, 0, home, 0, empty, p, alive, sk.err)) mode = 0;
-        else if (source_allowed(R, Q, home) && refill_source(R, Q, empty, p, alive, sk)) mode = src_type;
-        else if (refill_queue(Q, 1, home, kStealProbes, empty, p, alive, sk.err)) mode = 1;
-        else if (refill_queue(Q, 0, home, kStealProbes, empty, p, alive, sk.err)) mode = 0;
-      } else if (mode == src_type) {
-        // while the CTA's shards are filling up, let these lanes drain so
-        // that the warp turns to the secondaries
-        if (source_allowed(R, Q, home) && !refill_queue(Q, mode, home, 0, empty, p, alive, sk.err))
-          refill_source(R, Q, empty, p, alive, sk);
-      } else {
-        refill_queue(Q, mode, home, kStealProbes, empty, p, alive, sk.err);
+        if (ph == 1) {
+          if (refill_queue(Q, O, home, 0, empty, p, alive, sk.err)) mode = O;
+          else if (refill_queue(Q, O, home, kStealProbes, empty, p, alive, sk.err)) mode = O;
+          else if (refill_queue(Q, S, home, 0, empty, p, alive, sk.err)) mode = S;
+          else if (refill_queue(Q, S, home, kStealProbes, empty, p, alive, sk.err)) mode = S;
+        } else {
+          int ty = S;
+          if (refill_queue(Q, S, home, 0, empty, p, alive, sk.err)) mode = S;
+          else if (source_allowed(Q, home, Q.guard[S]) && refill_source<kMulti>(R, Q, empty, p, alive, sk, ty)) mode = S;
+          else if (refill_queue(Q, O, home, 0, empty, p, alive, sk.err)) mode = O;
+          else if (refill_queue(Q, O, home, kStealProbes, empty, p, alive, sk.err)) mode = O;
+          else if (refill_queue(Q, S, home, kStealProbes, empty, p, alive, sk.err)) mode = S;
+        }
+      } else if (mode == S) {
+        int ty = S;
+        if (ph == 0 && !refill_queue(Q, S, home, 0, empty, p, alive, sk.err) && source_allowed(Q, home, Q.guard[S]))
+          refill_source<kMulti>(R, Q, empty, p, alive, sk, ty);
+      } else if (ph == 1 || source_exhausted<kMulti>(R, Q)) {
+        refill_queue(Q, O, home, kStealProbes, empty, p, alive, sk.err);
       }
       if (alive && !was_alive) {
-        sk.slab = R.slabs + (uint64_t(p.hist) / Q.batch_size) * V;
+        if (kMulti) {
+          const DevJob &J = R.jobs[p.job];
+          sk.slab = J.slabs + (uint64_t(p.hist) / J.batch_size) * J.V;
+        } else {
+          sk.slab = R.slabs + (uint64_t(p.hist) / Q.batch_size) * V;
+        }
         nstep = 0;
       }
       live = __ballot_sync(kFull, alive);
@@ -388,7 +535,7 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS) k_queue(const _
         idle = true;
         idle_t0 = now_ns();
       }
-      if (any_work(R, Q)) {
+      if (any_work<kMulti>(R, Q)) {
         if (lane == 0) atomicAdd(&Q.idle->v, ~0ull);  // -1
         idle = false;
         sleep_ns = 128;
@@ -403,7 +550,7 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS) k_queue(const _
       done = __shfl_sync(kFull, done, 0);
       if (done) {
         __threadfence();
-        if (!any_work(R, Q)) break;
+        if (!any_work<kMulti>(R, Q)) break;
       }
       const bool expired = __shfl_sync(kFull, now_ns() - idle_t0 > Q.timeout_ns, 0);
       if (expired) {
@@ -416,17 +563,17 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS) k_queue(const _
     }
     if (alive) {
       if (mode == 0) {
-        alive = photon_segment(p, R, sk);
+        alive = kMulti ? photon_segment(p, job_ctx(R, p.job), sk) : photon_segment(p, R, sk);
         if (alive && ++nstep >= kMaxPhotonSegments) {
           sk.error(ERR_STEPCAP);
-          sk.deposit(vox(p, R.P), p.E);
+          sk.deposit(kMulti ? vox(p, R.jobs[p.job].P) : vox(p, R.P), p.E);
           alive = false;
         }
       } else {
-        alive = electron_step(p, R, sk);
+        alive = kMulti ? electron_step(p, job_ctx(R, p.job), sk) : electron_step(p, R, sk);
         if (alive && ++nstep >= kMaxElectronSteps) {
           sk.error(ERR_STEPCAP);
-          sk.deposit(vox(p, R.P), p.E);
+          sk.deposit(kMulti ? vox(p, R.jobs[p.job].P) : vox(p, R.P), p.E);
           alive = false;
         }
       }
@@ -449,32 +596,41 @@ __global__ void k_queue_init(uint32_t *seq0, uint32_t *seq1, size_t n, uint32_t 
 int queue_blocks_per_sm() {
   // the kernel keeps no shared memory: give the whole carveout to L1, where
   // the tables are cached
-  cudaFuncSetAttribute(k_queue, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_queue, kQBlock, 0) != cudaSuccess) {
+  cudaFuncSetAttribute(k_queue<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_queue<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  int per_sm = 0, per_sm_multi = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_queue<false>, kQBlock, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_multi, k_queue<true>, kQBlock, 0) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  return per_sm;
+  return std::min(per_sm, per_sm_multi);
 }
+
+constexpr int kWordsPerSlot = 13;  // x y z u v w E, voxel, id lo, id hi, history, job, sequence
+constexpr int kCtlWords = 8 + kMaxJobs;  // next_hist idle started cur_job[2] backlog[2] phase, job_next[kMaxJobs]
 
 size_t queue_bytes(int K, int log2cs) {
   const size_t slots = size_t(K) << log2cs;
-  const size_t per_type = slots * 12 * sizeof(uint32_t) + 2 * size_t(K) * sizeof(Ctl);
-  return 2 * per_type + 3 * sizeof(Ctl) + 128;
+  const size_t per_type = slots * kWordsPerSlot * sizeof(uint32_t) + 2 * size_t(K) * sizeof(Ctl);
+  return 2 * per_type + kCtlWords * sizeof(Ctl) + 128;
 }
 
 int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batch_size, const dpm_run_opts &o,
                  int sm_count, cudaStream_t st, cudaEvent_t start, std::string &err) {
   const size_t cs = size_t(1) << log2cs;
   const size_t slots = size_t(K) * cs;
-  const size_t per_type = slots * 12 * sizeof(uint32_t) + 2 * size_t(K) * sizeof(Ctl);
+  const size_t per_type = slots * kWordsPerSlot * sizeof(uint32_t) + 2 * size_t(K) * sizeof(Ctl);
   QDev Q{};
   char *m = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(mem) + 127) & ~uintptr_t(127));
   Q.next_hist = reinterpret_cast<Ctl *>(m);
   Q.idle = Q.next_hist + 1;
   Q.started = Q.next_hist + 2;
-  char *ctl_end = m + 3 * sizeof(Ctl);
+  Q.cur_job = Q.next_hist + 3;  // two words
+  Q.backlog = Q.next_hist + 5;  // two words
+  Q.phase = Q.next_hist + 7;
+  Q.job_next = Q.next_hist + 8;
+  char *ctl_end = m + kCtlWords * sizeof(Ctl);
   for (int t = 0; t < 2; ++t) {
     QType &T = Q.q[t];
     char *b = ctl_end + t * per_type;
@@ -487,13 +643,19 @@ int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batc
     T.idl = f + 8 * slots;
     T.idh = f + 9 * slots;
     T.hist = f + 10 * slots;
-    T.seq = f + 11 * slots;
+    T.job = f + 11 * slots;
+    T.seq = f + 12 * slots;
   }
   Q.K = K;
   Q.log2cs = log2cs;
   Q.mask = uint32_t(cs - 1);
   Q.refill_min = o.refill_min > 0 ? std::min(o.refill_min, 32) : 8;
-  Q.high_water = uint32_t(cs / 4);
+  Q.guard[0] = uint32_t(cs >> DPM_PHASE_GUARD_SHIFT_G);
+  Q.guard[1] = uint32_t(cs >> DPM_PHASE_GUARD_SHIFT_E);
+  Q.phase_high[0] = (long long)K * (long long)(cs >> DPM_PHASE_HIGH_SHIFT_G);
+  Q.phase_low[0] = (long long)K * (long long)(cs >> DPM_PHASE_LOW_SHIFT_G);
+  Q.phase_high[1] = (long long)K * (long long)(cs >> DPM_PHASE_HIGH_SHIFT_E);
+  Q.phase_low[1] = (long long)K * (long long)(cs >> DPM_PHASE_LOW_SHIFT_E);
   Q.limit = uint32_t(cs - 64);
   if (o.queue_limit > 0) Q.limit = std::min<uint32_t>(Q.limit, uint32_t(o.queue_limit));
   const double tmo = o.timeout_s > 0 ? o.timeout_s : 20.0;
@@ -502,8 +664,9 @@ int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batc
   // cost of a 20 MeV electron history on this path)
   Q.deadline_ns = Q.timeout_ns + (unsigned long long)(double(R.n) * 2000.0);
   Q.batch_size = batch_size;
-  // zero the control words of both types and the three run counters
-  cudaError_t e = cudaMemsetAsync(m, 0, 3 * sizeof(Ctl), st);
+  // zero the control words of both types and the run counters
+  const int n_ctl = R.jobs ? 8 + R.n_jobs : 8;
+  cudaError_t e = cudaMemsetAsync(m, 0, n_ctl * sizeof(Ctl), st);
   for (int t = 0; t < 2 && e == cudaSuccess; ++t) e = cudaMemsetAsync(Q.q[t].head, 0, 2 * size_t(K) * sizeof(Ctl), st);
   if (e != cudaSuccess) {
     err = cudaGetErrorString(e);
@@ -511,7 +674,8 @@ int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batc
   }
   k_queue_init<<<sm_count * 4, 256, 0, st>>>(Q.q[0].seq, Q.q[1].seq, slots, Q.mask);
   if (start) cudaEventRecord(start, st);
-  k_queue<<<K, kQBlock, 0, st>>>(R, Q);
+  if (R.jobs) k_queue<true><<<K, kQBlock, 0, st>>>(R, Q);
+  else k_queue<false><<<K, kQBlock, 0, st>>>(R, Q);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = cudaGetErrorString(e);
@@ -520,20 +684,15 @@ int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batc
   return DPM_OK;
 }
 
-int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_run_opts &o, int sm_count,
-              cudaStream_t st, cudaEvent_t start, std::string &err) {
-  if (R.n > 0x7fffffffull) {
-    err = "the queue kernel takes at most 2^31-1 histories per call";
-    return DPM_EINVAL;
-  }
+int queue_prepare(QueueState &q, const dpm_run_opts &o, int sm_count, int &K, int &log2cs, std::string &err) {
   const int per_sm = queue_blocks_per_sm();
   if (per_sm < 1) {
     err = "occupancy query failed";
     return DPM_ECUDA;
   }
   const int bps = o.blocks_per_sm > 0 ? std::min(o.blocks_per_sm, per_sm) : per_sm;
-  const int K = sm_count * bps;
-  const int log2cs = o.queue_log2 > 0 ? o.queue_log2 : 14;
+  K = sm_count * bps;
+  log2cs = o.queue_log2 > 0 ? o.queue_log2 : 14;
   if (log2cs < 7 || log2cs > 20) {
     err = "queue_log2 must be in [7, 20]";
     return DPM_EINVAL;
@@ -552,6 +711,22 @@ int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_
     q.bytes = bytes;
   }
   q.log2_cap = log2cs;
+  return DPM_OK;
+}
+
+int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_run_opts &o, int sm_count,
+              cudaStream_t st, cudaEvent_t start, std::string &err) {
+  if (R.n > 0x7fffffffull) {
+    err = "the queue kernel takes at most 2^31-1 histories per call";
+    return DPM_EINVAL;
+  }
+  if (R.jobs && (R.n_jobs < 1 || R.n_jobs > kMaxJobs)) {
+    err = "bad job count";
+    return DPM_EINVAL;
+  }
+  int K = 0, log2cs = 0;
+  const int rc = queue_prepare(q, o, sm_count, K, log2cs, err);
+  if (rc) return rc;
   return queue_launch(q.mem, K, log2cs, R, batch_size, o, sm_count, st, start, err);
 }
 

@@ -21,6 +21,10 @@ int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_
               cudaStream_t st, cudaEvent_t start, std::string &err);
 void queue_free(QueueState &q);
 
+// Launch shape (K shards = blocks, 2^log2cs slots per shard) for the options,
+// and the context's queue memory allocated for it.
+int queue_prepare(QueueState &q, const dpm_run_opts &o, int sm_count, int &K, int &log2cs, std::string &err);
+
 // Resident blocks per SM of the queue kernel (occupancy query), or 0 on error.
 int queue_blocks_per_sm();
 // Device bytes the queues of K shards of 2^log2cs slots occupy.

@@ -49,7 +49,12 @@ class dpm_source(C.Structure):
 class dpm_run_opts(C.Structure):
     _fields_ = [("kernel", C.c_int), ("n_batches", C.c_int), ("block_size", C.c_int), ("blocks_per_sm", C.c_int),
                 ("queue_log2", C.c_int), ("refill_min", C.c_int), ("timeout_s", C.c_double),
-                ("physics_flags", C.c_int), ("queue_limit", C.c_int)]
+                ("physics_flags", C.c_int), ("queue_limit", C.c_int), ("use_graph", C.c_int)]
+
+
+class dpm_job(C.Structure):
+    _fields_ = [("phantom_id", C.c_int), ("src", dpm_source), ("first_history", C.c_uint64),
+                ("n_histories", C.c_uint64), ("seed", C.c_uint64)]
 
 
 class dpm_run_stats(C.Structure):
@@ -77,9 +82,12 @@ _SIGS = {
     "dpm_run": (C.c_int, [_P, C.c_int, C.POINTER(dpm_source), C.c_uint64, C.c_uint64, C.c_uint64,
                           C.POINTER(dpm_run_opts)]),
     "dpm_reset_tally": (C.c_int, [_P, C.c_int]),
+    "dpm_run_batch": (C.c_int, [_P, _P, C.c_int, C.POINTER(dpm_run_opts)]),
+    "dpm_batch_stats": (C.c_int, [_P, C.POINTER(dpm_run_stats)]),
     "dpm_read_dose": (C.c_int, [_P, C.c_int, _P, _P, _P, C.POINTER(dpm_run_stats)]),
     "dpm_read_dose_device": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(dpm_run_stats)]),
     "dpm_sync": (C.c_int, [_P]),
+    "dpm_dmax_sigma": (C.c_int, [_P, _P, C.c_int, _P]),
     "dpm_diag_table": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
     "dpm_diag_sample": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, _P, _P]),
     "dpm_diag_philox": (C.c_int, [_P, C.c_int, _P, _P, _P]),
@@ -214,6 +222,14 @@ def dpm_read_dose_device(ctx, pid: int, dose_t, sigma_t):
     return st.as_dict()
 
 
+def dpm_dmax_sigma(ctx, pids) -> np.ndarray:
+    """[(dose_max Gy/history, sigma, voxel index)] for each phantom id."""
+    ids = np.ascontiguousarray(pids, np.int32)
+    out = np.zeros((len(ids), 3), np.float64)
+    _check(ctx, lib().dpm_dmax_sigma(ctx, _ptr(ids), len(ids), _ptr(out)))
+    return out
+
+
 def dpm_sync(ctx):
     _check(ctx, lib().dpm_sync(ctx))
 
@@ -245,9 +261,23 @@ def dpm_diag_philox(ctx, ctr, key) -> np.ndarray:
 
 
 def run_opts(kernel=KERNEL_QUEUE, n_batches=0, block_size=0, blocks_per_sm=0, queue_log2=0, refill_min=0,
-             timeout_s=0.0, physics_flags=0, queue_limit=0) -> dpm_run_opts:
+             timeout_s=0.0, physics_flags=0, queue_limit=0, use_graph=0) -> dpm_run_opts:
     return dpm_run_opts(kernel, n_batches, block_size, blocks_per_sm, queue_log2, refill_min, timeout_s,
-                        physics_flags, queue_limit)
+                        physics_flags, queue_limit, int(use_graph))
+
+
+def dpm_run_batch(ctx, jobs, opts: dpm_run_opts | None = None):
+    """``jobs``: list of (phantom_id, Source, first_history, n_histories, seed)."""
+    arr = (dpm_job * max(len(jobs), 1))()
+    for k, (pid, src, first, n, seed) in enumerate(jobs):
+        arr[k] = dpm_job(pid, source_struct(src), first, n, seed)
+    _check(ctx, lib().dpm_run_batch(ctx, arr, len(jobs), C.byref(opts) if opts is not None else None))
+
+
+def dpm_batch_stats(ctx) -> dict:
+    st = dpm_run_stats()
+    _check(ctx, lib().dpm_batch_stats(ctx, C.byref(st)))
+    return st.as_dict()
 
 
 class Dpm:

@@ -220,3 +220,26 @@ WORKLOADS = {
     "6mv_wbw_61x61x60": c1_photon_wbw,
     "e20_blob128": c2_electron_blob128,
 }
+
+
+def c3_batch(scale=1.0, n_jobs=64, seed=0):
+    """64 jobs for one batched launch: sizes uniform over {64^3, 96^3, 128^3,
+    256x256x128} voxels of U[0.2, 0.5] cm with seeded blob densities (phantom
+    seed 1000+i); even jobs a synthetic 6 MV beam, odd jobs monoenergetic
+    electrons of 6..20 MeV; 10x10 cm field, SSD 90 cm; 10^U[5,7] histories
+    (times `scale`); run seed 2000+i.  Returns [(Phantom, Source, n, seed)]."""
+    g = SplitMix64(0xC3 + seed)
+    sizes = [(64, 64, 64), (96, 96, 96), (128, 128, 128), (256, 256, 128)]
+    out = []
+    for i in range(n_jobs):
+        nx, ny, nz = sizes[min(int(g.uniform() * 4), 3)]
+        d = round(0.2 + 0.3 * g.uniform(), 3)
+        ph = blob_phantom(nx, ny, nz, d, 1000 + i, name=f"batch{i}_{nx}x{ny}x{nz}")
+        if i % 2 == 0:
+            src = axial_source(ph, PHOTON, SPEC_6MV, 6.0, ssd=90.0, sad=100.0, fx=10.0, fy=10.0)
+        else:
+            e = float(6 + min(int(g.uniform() * 15), 14))
+            src = axial_source(ph, ELECTRON, SPEC_MONO, e, ssd=90.0, sad=100.0, fx=10.0, fy=10.0)
+        n = max(1, int(round(10 ** (5 + 2 * g.uniform()) * scale)))
+        out.append((ph, src, n, 2000 + i))
+    return out

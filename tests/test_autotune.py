@@ -1,0 +1,25 @@
+"""CPU tests of the autotuner's search and cache (no GPU)."""
+from paper_0910_0329_gb300 import autotune
+
+
+def test_coordinate_descent_finds_separable_optimum():
+    target = {"queue_log2": 13, "blocks_per_sm": 6, "refill_min": 16}
+    calls = []
+
+    def trial(o):
+        calls.append(o)
+        return 1.0 + sum((o[k] - target[k]) ** 2 for k in target) * 0.01
+
+    best, t, log = autotune.coordinate_descent(trial, autotune.DEFAULT_SPACE, autotune.DEFAULT_START)
+    assert best == target
+    assert t == 1.0
+    assert len(calls) == len(log) < 4 * 3 * 3  # fewer trials than the full grid, none repeated
+
+
+def test_cache_roundtrip(tmp_path):
+    p = str(tmp_path / "t.json")
+    k = autotune.signature("GB300", "batch64")
+    assert autotune.load(k, p) is None
+    autotune.save(k, {"opts": {"refill_min": 4}}, p)
+    autotune.save("other", {"opts": {}}, p)
+    assert autotune.load(k, p)["opts"] == {"refill_min": 4}
