@@ -108,9 +108,11 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profiled_traffic(kernel: str, workload: str):
-    """DRAM bytes per history of `kernel` from the committed ncu summary, if the
-    kernel's source has not changed since the capture (else None)."""
+def profiled_traffic(kernel: str, workload: str, key: str = "traffic_bytes_per_history"):
+    """Bytes per history of `kernel` (DRAM traffic, or with key
+    l2_bytes_per_history the L1->L2 sector traffic) from the committed ncu
+    summary, if the kernel's source has not changed since the capture (else
+    None)."""
     import hashlib
     import re
 
@@ -119,7 +121,7 @@ def profiled_traffic(kernel: str, workload: str):
         return None
     text = open(path).read()
     fp = re.search(r"first 16 hex digits\): `([0-9a-f]{16})`", text)
-    tb = re.search(r"traffic_bytes_per_history: ([0-9.]+)", text)
+    tb = re.search(key + r": ([0-9.]+)", text)
     if not fp or not tb:
         return None
     src = os.path.join(ROOT, "paper_0910_0329_gb300", "csrc")
@@ -301,6 +303,22 @@ def main():
             "roofline": roof, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
             "wall_s_timed_region": wall,
             "energy_balance_rel": abs(st["emitted"] - st["deposited"] - st["escaped"] - st["missed"]) / st["emitted"]}
+
+    # L2 roofline: the tally's scattered 64-bit atomics and the L1->L2 sector
+    # traffic (per history, from the committed ncu capture) against this GPU's
+    # L2 ceilings measured now by dpm_diag_l2_peaks
+    atom_pk, l2_pk = dpm.dpm_diag_l2_peaks(d.ctx, 16 << 20)
+    atom_rate = atom_per_hist * hist_per_launch / t_kernel_s
+    l2_bph = profiled_traffic(kname, args.workload, "l2_bytes_per_history")
+    l2_rate = l2_bph * hist_per_launch / t_kernel_s if l2_bph else None
+    line["l2_roofline"] = {
+        "atomics": {"achieved": atom_rate, "peak": atom_pk, "unit": "atomics/s", "frac": atom_rate / atom_pk,
+                    "what": "tally atomics of the transport kernel vs scattered 64-bit atomics over 16 MiB"},
+        "bandwidth": {"achieved": l2_rate / 1e9 if l2_rate else None, "peak": l2_pk / 1e9, "unit": "GB/s",
+                      "frac": l2_rate / l2_pk if l2_rate else None, "bytes_per_history": l2_bph,
+                      "what": "L1->L2 sectors per history (ncu capture of this kernel) vs L1-bypassing loads "
+                              "swept over 16 MiB"},
+        "peak_kind": "measured (dpm_diag_l2_peaks, this run)"}
 
     if not args.no_e2e:
         line["e2e"] = e2e(args, d, wl, n, kernel, local)

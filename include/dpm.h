@@ -214,6 +214,17 @@ int dpm_diag_sample(dpm_ctx *ctx, int which, double e, double aux, int n, const 
 /* n Philox4x32-10 blocks for counters ctr[4*i..] and keys key[2*i..] (host). */
 int dpm_diag_philox(dpm_ctx *ctx, int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out);
 
+/* L2 ceilings of this GPU for the roofline of the transport kernel (not a
+   step of the paper's method).  Over a device buffer of ws_bytes (a power of
+   two in [1 MiB, 64 MiB], small enough to stay in L2; the call allocates and
+   frees it) it times, after a warm-up launch of each:
+     out[0]  scattered 64-bit atomic adds per second (xorshift32 addresses,
+             the access pattern of the voxel tally);
+     out[1]  bytes per second of 16-byte loads that bypass L1, swept 16 times
+             over the buffer.
+   Synchronous.  DPM_EINVAL for a bad size or a null out (host, 2 doubles). */
+int dpm_diag_l2_peaks(dpm_ctx *ctx, uint64_t ws_bytes, double *out);
+
 /* ---- transport without device allocation -------------------------------
    Not a step of the paper's method (the paper has no counterpart): an entry
    point for callers that cannot allocate device memory once they are running,

@@ -592,4 +592,45 @@ int dpm_diag_philox(dpm_ctx *c, int n, const uint32_t *ctr, const uint32_t *key,
   return DPM_OK;
 }
 
+int dpm_diag_l2_peaks(dpm_ctx *c, uint64_t ws_bytes, double *out) {
+  if (!c) return DPM_EINVAL;
+  if (!out || ws_bytes < (1u << 20) || ws_bytes > (64u << 20) || (ws_bytes & (ws_bytes - 1)))
+    return fail(c, DPM_EINVAL, "ws_bytes must be a power of two in [1 MiB, 64 MiB]");
+  cudaSetDevice(c->device);
+  char *d = nullptr;
+  int rc = dalloc(c, &d, size_t(ws_bytes) + 256);
+  if (rc) return rc;
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) cudaEventCreate(&ev[i]);
+  unsigned long long *a = reinterpret_cast<unsigned long long *>(d);
+  const uint32_t mask = uint32_t(ws_bytes / 8 - 1);
+  const int blocks = c->sm_count * 8;
+  const int iters = 256;
+  float *sink = reinterpret_cast<float *>(d + ws_bytes);
+  const size_t n4 = size_t(ws_bytes) / 16;
+  const int passes = 16;
+  cudaMemsetAsync(d, 0, size_t(ws_bytes) + 256, c->stream);
+  // warm-up (brings the buffer into L2), then one timed launch of each
+  launch_l2_atomic(a, mask, iters, blocks, c->stream);
+  launch_l2_read(reinterpret_cast<const float4 *>(d), n4, 2, sink, blocks, c->stream);
+  cudaEventRecord(ev[0], c->stream);
+  launch_l2_atomic(a, mask, iters, blocks, c->stream);
+  cudaEventRecord(ev[1], c->stream);
+  cudaMemsetAsync(d, 0, size_t(ws_bytes), c->stream);
+  launch_l2_read(reinterpret_cast<const float4 *>(d), n4, 2, sink, blocks, c->stream);
+  cudaEventRecord(ev[2], c->stream);
+  launch_l2_read(reinterpret_cast<const float4 *>(d), n4, passes, sink, blocks, c->stream);
+  cudaEventRecord(ev[3], c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  float t_atom = 0.f, t_read = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t_atom, ev[0], ev[1]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t_read, ev[2], ev[3]);
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(c, DPM_ECUDA, cudaGetErrorString(e));
+  out[0] = double(blocks) * 256.0 * iters / (t_atom * 1e-3);
+  out[1] = double(ws_bytes) * passes / (t_read * 1e-3);
+  return DPM_OK;
+}
+
 }  // extern "C"

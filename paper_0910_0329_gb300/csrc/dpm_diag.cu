@@ -94,4 +94,38 @@ void launch_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_
   k_diag_philox<<<(n + 127) / 128, 128, 0, st>>>(n, ctr, key, out);
 }
 
+// L2 ceilings of the tally and table traffic, measured on the GPU at hand.
+// Atomics: each thread adds 1 to `iters` addresses drawn by xorshift32 over
+// a power-of-two array (scattered 64-bit adds, the access pattern of the
+// voxel tally).  Reads: 16-byte loads that bypass L1, swept `passes` times
+// over an L2-resident buffer.
+__global__ void k_l2_atomic(unsigned long long *a, uint32_t mask, int iters) {
+  uint32_t x = ((blockIdx.x * blockDim.x + threadIdx.x) * 0x9E3779B9u) | 1u;
+  for (int k = 0; k < iters; ++k) {
+    x ^= x << 13;
+    x ^= x >> 17;
+    x ^= x << 5;
+    atomicAdd(a + (x & mask), 1ull);
+  }
+}
+
+__global__ void k_l2_read(const float4 *b, size_t n, int passes, float *sink) {
+  float acc = 0.f;
+  const size_t stride = size_t(gridDim.x) * blockDim.x;
+  for (int q = 0; q < passes; ++q)
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+      const float4 v = __ldcg(b + i);
+      acc += v.x + v.y + v.z + v.w;
+    }
+  if (acc == 1.2345e-30f) *sink = acc;  // never true for the zeroed buffer; keeps the loads
+}
+
+void launch_l2_atomic(unsigned long long *a, uint32_t mask, int iters, int blocks, cudaStream_t st) {
+  k_l2_atomic<<<blocks, 256, 0, st>>>(a, mask, iters);
+}
+
+void launch_l2_read(const float4 *b, size_t n, int passes, float *sink, int blocks, cudaStream_t st) {
+  k_l2_read<<<blocks, 256, 0, st>>>(b, n, passes, sink);
+}
+
 }  // namespace dpm

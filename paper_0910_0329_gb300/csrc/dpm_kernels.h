@@ -22,5 +22,7 @@ void launch_diag_table(const DevTables &T, const DevPhantom &P, int which, int m
 void launch_diag_sample(const DevTables &T, int which, double e, double aux, int n, const double *u, double *out,
                         cudaStream_t st);
 void launch_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, cudaStream_t st);
+void launch_l2_atomic(unsigned long long *a, uint32_t mask, int iters, int blocks, cudaStream_t st);
+void launch_l2_read(const float4 *b, size_t n, int passes, float *sink, int blocks, cudaStream_t st);
 
 }  // namespace dpm

@@ -91,6 +91,7 @@ _SIGS = {
     "dpm_diag_table": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
     "dpm_diag_sample": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, _P, _P]),
     "dpm_diag_philox": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "dpm_diag_l2_peaks": (C.c_int, [_P, C.c_uint64, _P]),
     "dpm_run_noalloc": (C.c_int, [_P, C.c_int, C.POINTER(dpm_source), C.c_uint64, C.c_uint64, C.c_uint64, _P]),
     # include/dpm_host.h (host-only table inspection)
     "dpm_host_tables_build": (_P, [C.POINTER(dpm_material), C.c_int, C.POINTER(dpm_table_params), C.c_char_p]),
@@ -258,6 +259,14 @@ def dpm_diag_philox(ctx, ctr, key) -> np.ndarray:
     out = np.zeros(4 * n, np.uint32)
     _check(ctx, lib().dpm_diag_philox(ctx, n, _ptr(c), _ptr(k), _ptr(out)))
     return out.reshape(n, 4)
+
+
+def dpm_diag_l2_peaks(ctx, ws_bytes=16 << 20):
+    """(scattered 64-bit atomic adds per second, L2 read bytes per second)
+    over an L2-resident buffer of ws_bytes."""
+    out = np.zeros(2, np.float64)
+    _check(ctx, lib().dpm_diag_l2_peaks(ctx, int(ws_bytes), _ptr(out)))
+    return float(out[0]), float(out[1])
 
 
 def run_opts(kernel=KERNEL_QUEUE, n_batches=0, block_size=0, blocks_per_sm=0, queue_log2=0, refill_min=0,
