@@ -117,6 +117,8 @@ typedef struct {
                                      (CUDA events recorded around each launch on its stream) */
     double fold_ms;               /* device time of the batch folds of those runs */
     uint64_t n_transport_launches;/* transport kernel launches since the previous read */
+    uint64_t n_phase_switches;    /* queue kernel: grid-wide switches between the source phase and
+                                     the secondary phase (0 for the per-history kernel) */
 } dpm_run_stats;
 
 int dpm_create(dpm_ctx **out, int cuda_device);

@@ -143,9 +143,9 @@ extern "C" int dpm_run_batch(dpm_ctx *c, const dpm_job *jobs, int n_jobs, const 
   }
   if (!c->d_jobs && (rc = ctx_alloc(c, reinterpret_cast<void **>(&c->d_jobs), kMaxJobs * sizeof(DevJob)))) return rc;
   if (!c->d_batch_counters) {
-    if ((rc = ctx_alloc(c, reinterpret_cast<void **>(&c->d_batch_counters), C_N * sizeof(unsigned long long))))
+    if ((rc = ctx_alloc(c, reinterpret_cast<void **>(&c->d_batch_counters), kCounterSlots * sizeof(unsigned long long))))
       return rc;
-    BATCH_TRY(c, cudaMemsetAsync(c->d_batch_counters, 0, C_N * sizeof(unsigned long long), c->stream));
+    BATCH_TRY(c, cudaMemsetAsync(c->d_batch_counters, 0, kCounterSlots * sizeof(unsigned long long), c->stream));
   }
   // the job table is read by the kernel at run time (also on graph replays)
   if (!b.tab.empty())
@@ -247,7 +247,7 @@ extern "C" int dpm_batch_stats(dpm_ctx *c, dpm_run_stats *st) {
   std::memset(st, 0, sizeof(*st));
   st->n_histories = c->batch_histories;
   if (c->d_batch_counters) {
-    unsigned long long cnt[C_N];
+    unsigned long long cnt[kCounterSlots];
     BATCH_TRY(c, cudaMemcpy(cnt, c->d_batch_counters, sizeof(cnt), cudaMemcpyDeviceToHost));
     BATCH_TRY(c, cudaMemset(c->d_batch_counters, 0, sizeof(cnt)));
     st->emitted = double((long long)cnt[C_EMIT]) / kTallyScale;
@@ -258,6 +258,7 @@ extern "C" int dpm_batch_stats(dpm_ctx *c, dpm_run_stats *st) {
     st->n_g_interactions = cnt[C_GINT];
     st->n_tally_atomics = cnt[C_ATOM];
     st->n_pushed = cnt[C_PUSH];
+    st->n_phase_switches = cnt[C_SWITCH];
   }
   for (size_t i = 0; i + 1 < c->batch_ev.size(); i += 2) {
     float ms = 0;

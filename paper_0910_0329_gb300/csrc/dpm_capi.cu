@@ -264,7 +264,7 @@ int dpm_load_phantom(dpm_ctx *c, int nx, int ny, int nz, double dx, double dy, d
   }
   int rc;
   if ((rc = dalloc(c, &p->d_mat, p->V)) || (rc = dalloc(c, &p->d_rho, p->V)) || (rc = dalloc(c, &p->d_S1, p->V)) ||
-      (rc = dalloc(c, &p->d_Q, p->V)) || (rc = dalloc(c, &p->d_counters, size_t(C_N))) ||
+      (rc = dalloc(c, &p->d_Q, p->V)) || (rc = dalloc(c, &p->d_counters, size_t(kCounterSlots))) ||
       (rc = dalloc(c, &p->d_inv_nb, size_t(1024))) || (rc = dalloc(c, &p->d_mumax, size_t(kMaxTableNodes)))) {
     free_phantom(p.get());
     return rc;
@@ -273,7 +273,7 @@ int dpm_load_phantom(dpm_ctx *c, int nx, int ny, int nz, double dx, double dy, d
   CUDA_TRY(c, cudaMemcpyAsync(p->d_rho, rho, p->V * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(p->d_S1, 0, p->V * sizeof(long long), c->stream));
   CUDA_TRY(c, cudaMemsetAsync(p->d_Q, 0, p->V * sizeof(double), c->stream));
-  CUDA_TRY(c, cudaMemsetAsync(p->d_counters, 0, C_N * sizeof(unsigned long long), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(p->d_counters, 0, kCounterSlots * sizeof(unsigned long long), c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if ((rc = update_mumax(c, p.get()))) {
     free_phantom(p.get());
@@ -351,7 +351,7 @@ int dpm_reset_tally(dpm_ctx *c, int id) {
   cudaSetDevice(c->device);
   CUDA_TRY(c, cudaMemsetAsync(p->d_S1, 0, p->V * sizeof(long long), c->stream));
   CUDA_TRY(c, cudaMemsetAsync(p->d_Q, 0, p->V * sizeof(double), c->stream));
-  CUDA_TRY(c, cudaMemsetAsync(p->d_counters, 0, C_N * sizeof(unsigned long long), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(p->d_counters, 0, kCounterSlots * sizeof(unsigned long long), c->stream));
   p->n_total = 0;
   p->b_total = 0;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -445,7 +445,7 @@ int dpm_sync(dpm_ctx *c) {
 // Fill the run summary; s1_host (if not NULL) already holds the integer tally.
 static int read_common(dpm_ctx *c, PhantomState *p, const int64_t *s1_host, dpm_run_stats *st, int sync_rc) {
   if (st) {
-    unsigned long long cnt[C_N];
+    unsigned long long cnt[kCounterSlots];
     CUDA_TRY(c, cudaMemcpy(cnt, p->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost));
     std::memset(st, 0, sizeof(*st));
     st->n_histories = p->n_total;
@@ -467,6 +467,7 @@ static int read_common(dpm_ctx *c, PhantomState *p, const int64_t *s1_host, dpm_
     st->n_g_interactions = cnt[C_GINT];
     st->n_tally_atomics = cnt[C_ATOM];
     st->n_pushed = cnt[C_PUSH];
+    st->n_phase_switches = cnt[C_SWITCH];
     for (size_t i = 0; i + 2 < p->ev.size(); i += 3) {
       float a = 0, b = 0;
       if (cudaEventElapsedTime(&a, p->ev[i], p->ev[i + 1]) == cudaSuccess) st->transport_ms += a;

@@ -57,7 +57,7 @@ struct dpm_ctx {
   dpm::QueueState queue;
   // batches
   dpm::DevJob *d_jobs = nullptr;               // job table, kMaxJobs entries
-  unsigned long long *d_batch_counters = nullptr;  // [C_N]
+  unsigned long long *d_batch_counters = nullptr;  // [kCounterSlots]
   std::vector<cudaEvent_t> batch_ev;           // start/end pairs since the last dpm_batch_stats
   uint64_t batch_histories = 0;
   cudaGraphExec_t batch_exec = nullptr;

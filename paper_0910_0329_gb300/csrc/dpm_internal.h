@@ -66,6 +66,10 @@ enum {
   C_ESTEP, C_GFLIGHT, C_GINT, C_ATOM, C_PUSH,
   C_N
 };
+// One more device counter beyond the per-thread ones: grid phase switches of
+// the queue kernel (counted by the warp that switches).
+constexpr int C_SWITCH = C_N;
+constexpr int kCounterSlots = C_N + 1;
 
 enum { ERR_OVERFLOW = 1, ERR_STEPCAP = 2, ERR_TIMEOUT = 4 };
 
@@ -91,7 +95,7 @@ struct RunParams {
   uint32_t key0, key1;     // Philox key from the seed
   int n_batches;
   unsigned long long *slabs;  // [n_batches][V]
-  unsigned long long *counters;  // [C_N] (energies as two's-complement int64)
+  unsigned long long *counters;  // [kCounterSlots] (energies as two's-complement int64)
   int *err;
   const DevJob *jobs;  // batch launches only: the job table (global memory)
   int n_jobs;

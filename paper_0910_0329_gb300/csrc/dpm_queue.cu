@@ -407,17 +407,17 @@ __device__ bool source_allowed(const QDev &Q, int home, unsigned long long bound
 // The grid-wide phase (0 source, 1 secondary) for beam type S, switched
 // with hysteresis on the global backlog of the other type by whichever warp
 // sees the threshold crossed first (warp-uniform).
-__device__ int grid_phase(const QDev &Q, int S) {
+__device__ int grid_phase(const QDev &Q, int S, unsigned long long *counters) {
   int ph = 0;
   if ((threadIdx.x & 31) == 0) {
     ph = int(ld_volatile(&Q.phase->v));
     const long long b = (long long)ld_volatile(&Q.backlog[1 - S].v);
     if (ph == 0 && b > Q.phase_high[S]) {
       ph = 1;
-      *(volatile unsigned long long *)&Q.phase->v = 1ull;
+      if (atomicExch(&Q.phase->v, 1ull) == 0ull) atomicAdd(counters + C_SWITCH, 1ull);
     } else if (ph == 1 && b < Q.phase_low[S]) {
       ph = 0;
-      *(volatile unsigned long long *)&Q.phase->v = 0ull;
+      if (atomicExch(&Q.phase->v, 0ull) == 1ull) atomicAdd(counters + C_SWITCH, 1ull);
     }
   }
   return __shfl_sync(kFull, ph, 0);
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
       // finish their lanes and turn over.  A grid-wide phase keeps the SMs
       // on one of the two code paths at a time.
       const int O = 1 - S;
-      const int ph = grid_phase(Q, S);
+      const int ph = grid_phase(Q, S, R.counters);
       if (mode < 0) {
         if (ph == 1) {
           if (refill_queue(Q, O, home, 0, empty, p, alive, sk.err)) mode = O;

@@ -62,7 +62,8 @@ class dpm_run_stats(C.Structure):
                 ("emitted", C.c_double), ("deposited", C.c_double), ("escaped", C.c_double), ("missed", C.c_double),
                 ("n_e_steps", C.c_uint64), ("n_g_flights", C.c_uint64), ("n_g_interactions", C.c_uint64),
                 ("n_tally_atomics", C.c_uint64), ("n_pushed", C.c_uint64), ("transport_ms", C.c_double),
-                ("fold_ms", C.c_double), ("n_transport_launches", C.c_uint64)]
+                ("fold_ms", C.c_double), ("n_transport_launches", C.c_uint64),
+                ("n_phase_switches", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -92,3 +92,23 @@ def test_batch_argument_errors():
         assert e.value.code == dpm.DPM_EINVAL
         dpm.dpm_run_batch(d.ctx, [])  # empty batch is a no-op
         dpm.dpm_run_batch(d.ctx, [(pid, spec[0][1], 0, 0, 1)])  # so is a job without histories
+
+
+def test_large_batch_with_phase_switches_equals_jobs_run_alone():
+    """Enough histories per job for the grid-wide phase to switch within the
+    batch, across photon-beam and electron-beam jobs."""
+    c1, c0 = W.c1_photon_wbw(), W.c0_electron_wlw()
+    blob = W.blob_phantom(64, 64, 64, 0.4, 23, name="blob64")
+    spec = [(c1.phantom, c1.source, 0, 3_000_000, 21),
+            (blob, W.axial_source(blob, W.PHOTON, W.SPEC_6MV, 6.0, 90.0, 100.0, 10.0, 10.0), 0, 3_000_000, 22),
+            (c0.phantom, c0.source, 0, 200_000, 23)]
+    ref = [alone(*j) for j in spec]
+    with dpm.Dpm(0, W.MATERIALS, PARAMS) as d:
+        pids = [d.load_phantom(j[0]) for j in spec]
+        jobs = [(pid, src, first, n, seed) for pid, (_, src, first, n, seed) in zip(pids, spec)]
+        dpm.dpm_run_batch(d.ctx, jobs, dpm.run_opts(queue_log2=12))
+        st = dpm.dpm_batch_stats(d.ctx)
+        raws = [d.read(pid)[2] for pid in pids]
+    assert st["error_flags"] == 0 and st["n_phase_switches"] >= 2
+    for got, r in zip(raws, ref):
+        assert np.array_equal(got, r)

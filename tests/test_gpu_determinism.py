@@ -66,3 +66,39 @@ def test_queue_launch_shape_does_not_change_the_tally(wl, shape):
     a = raw_tally(wl, 200000, kernel=dpm.KERNEL_QUEUE)
     b = raw_tally(wl, 200000, kernel=dpm.KERNEL_QUEUE, **shape)
     assert np.array_equal(a, b)
+
+
+def run_stats(wl, n, kernel, **opts):
+    with dpm.Dpm(0, W.MATERIALS, wl.params) as d:
+        pid = d.load_phantom(wl.phantom)
+        d.run(pid, wl.source, n, wl.seed, kernel=kernel, **opts)
+        _, _, raw, st = d.read(pid)
+    assert st["error_flags"] == 0
+    return raw, st
+
+
+@pytest.mark.parametrize("beam,queue_log2", [("photon", 9), ("photon", 10), ("photon", 12),
+                                              ("electron", 9)])
+def test_grid_phase_switches_do_not_change_the_tally(beam, queue_log2):
+    """The queue kernel alternates grid-wide between a source phase and a
+    secondary phase at thresholds proportional to the queue capacity; small
+    queues force many switches.  The tally must still equal the per-history
+    kernel's bit for bit."""
+    wl = W.c1_photon_wbw() if beam == "photon" else W.c0_electron_wlw()
+    n = 2_000_000 if beam == "photon" else 100_000
+    ref, st_h = run_stats(wl, n, dpm.KERNEL_HISTORY)
+    got, st_q = run_stats(wl, n, dpm.KERNEL_QUEUE, queue_log2=queue_log2)
+    assert st_h["n_phase_switches"] == 0
+    assert st_q["n_phase_switches"] >= 2
+    assert np.array_equal(got, ref)
+
+
+def test_full_size_photon_launch_equals_history_kernel():
+    """The benchmarked configuration (6 MV, 10^7 histories in one launch with
+    the default queue): several phase switches, same tally as the
+    one-history-per-thread kernel."""
+    wl = W.c1_photon_wbw()
+    ref, _ = run_stats(wl, wl.n_histories, dpm.KERNEL_HISTORY)
+    got, st = run_stats(wl, wl.n_histories, dpm.KERNEL_QUEUE)
+    assert st["n_phase_switches"] >= 2
+    assert np.array_equal(got, ref)
