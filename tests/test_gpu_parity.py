@@ -153,3 +153,45 @@ def test_straight_csda_track_matches_oracle(kernel):
     assert got.sum() == pytest.approx(20.0, rel=1e-6)
     # energy lost per voxel; the last voxel also takes the residual 200 keV
     np.testing.assert_allclose(got, ref, rtol=2e-4, atol=2e-4)
+
+
+@pytest.mark.parametrize("kernel", KERNELS, ids=["history", "queue"])
+@pytest.mark.parametrize("axis", ["x", "z"])
+def test_straight_track_across_the_largest_index_range(kernel, axis):
+    """A queued particle carries its voxel as 11 + 11 + 10 bits, so a phantom
+    may have up to 2047 x 2047 x 1023 voxels.  A straight 20 MeV pencil (no
+    hard events, no deflection) through 6 cm of water crosses every voxel of
+    a 2047-voxel row along x (gantry 90) or a 1023-voxel column along z and
+    leaves with its residual energy; the deposits follow the oracle's CSDA
+    profile voxel by voxel (compared cumulatively: each voxel holds a few keV)."""
+    n, L = (2047, 6.0) if axis == "x" else (1023, 6.0)
+    d = L / n
+    shape = (n, 1, 1) if axis == "x" else (1, 1, n)
+    sizes = (d, 0.2, 0.2) if axis == "x" else (0.2, 0.2, d)
+    ph = W.Phantom(*shape, *sizes, np.full(n, W.MAT_WATER, np.uint8), np.full(n, 1.0, np.float32))
+    if axis == "x":
+        src = W.Source(W.ELECTRON, W.SPEC_MONO, 20.0, (L / 2, 0.1, 0.1), 100.0, 1e-6, 1e-6, 90.0)
+    else:
+        src = W.Source(W.ELECTRON, W.SPEC_MONO, 20.0, (0.1, 0.1, L / 2), 100.0, 1e-6, 1e-6, 0.0)
+    orc = O.run(ph, W.MATERIALS, W.DEFAULT_PARAMS, src, 1, 1, workers=1, flags=O.OR_NO_HARD | O.OR_NO_MSC)
+    with dpm.Dpm(0, W.MATERIALS, W.DEFAULT_PARAMS) as d_:
+        pid = d_.load_phantom(ph)
+        d_.run(pid, src, 64, 1, kernel=kernel, physics_flags=dpm.NO_HARD | dpm.NO_MSC)
+        _, _, raw, st = d_.read(pid)
+    got = raw / 2.0 ** 32 / 64
+    ref = orc.S1
+    assert st["error_flags"] == 0
+    assert (got > 0).all() and (ref > 0).all()  # every index, up to the largest, was crossed
+    assert got.sum() + st["escaped"] / 64 == pytest.approx(20.0, rel=1e-6)
+    np.testing.assert_allclose(np.cumsum(got), np.cumsum(ref), rtol=2e-4, atol=2e-4)
+
+
+def test_phantom_size_limits(gpu_lib):
+    with dpm.Dpm(0, W.MATERIALS, W.DEFAULT_PARAMS) as d:
+        for shape in [(2048, 1, 1), (1, 2048, 1), (1, 1, 1024)]:
+            ph = W.Phantom(*shape, 0.1, 0.1, 0.1, np.zeros(int(np.prod(shape)), np.uint8),
+                           np.ones(int(np.prod(shape)), np.float32))
+            with pytest.raises(dpm.DpmError):
+                d.load_phantom(ph)
+        ok = W.Phantom(2047, 2, 3, 0.1, 0.1, 0.1, np.zeros(2047 * 6, np.uint8), np.ones(2047 * 6, np.float32))
+        d.load_phantom(ok)
