@@ -113,7 +113,6 @@ def profiled_traffic(kernel: str, workload: str, key: str = "traffic_bytes_per_h
     l2_bytes_per_history the L1->L2 sector traffic) from the committed ncu
     summary, if the kernel's source has not changed since the capture (else
     None)."""
-    import hashlib
     import re
 
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
@@ -124,12 +123,25 @@ def profiled_traffic(kernel: str, workload: str, key: str = "traffic_bytes_per_h
     tb = re.search(key + r": ([0-9.]+)", text)
     if not fp or not tb:
         return None
+    return float(tb.group(1)) if kernel_fingerprint() == fp.group(1) else None
+
+
+def kernel_fingerprint():
+    """First 16 hex digits of the sha256 of the transport kernel's sources
+    (dpm_device.cuh, dpm_queue.cu, dpm_internal.h) with comments and
+    whitespace removed: edits to comments keep a capture valid."""
+    import hashlib
+    import re
+
     src = os.path.join(ROOT, "paper_0910_0329_gb300", "csrc")
     h = hashlib.sha256()
     for f in ("dpm_device.cuh", "dpm_queue.cu", "dpm_internal.h"):
-        with open(os.path.join(src, f), "rb") as fh:
-            h.update(fh.read())
-    return float(tb.group(1)) if h.hexdigest()[:16] == fp.group(1) else None
+        with open(os.path.join(src, f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("".join(text.split()).encode())
+    return h.hexdigest()[:16]
 
 
 def run_reference(args, rank):

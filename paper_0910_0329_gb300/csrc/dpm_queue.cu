@@ -15,8 +15,10 @@
 // the consumer frees the slot for position p+capacity), so that producers and
 // consumers on different SMs never read a half-written record.  A warp pushes
 // to its CTA's shard and pops from it first, stealing from other shards when it
-// is empty.  The run ends when every started warp is idle, every queue is empty
-// and the source is exhausted.  Every wait is bounded by a time limit read from
+// is empty.  The grid alternates between a source phase and a secondary
+// phase (see the scheduler below) so that all SMs run one particle type's
+// code at a time.  The run ends when every started warp is idle, every queue
+// is empty and the source is exhausted.  Every wait is bounded by a time limit read from
 // %globaltimer; on expiry the kernel records an error and returns.
 #include <cuda_runtime.h>
 
@@ -79,8 +81,8 @@ struct QDev {
   Ctl *next_hist, *idle, *started;
   Ctl *backlog;   // queued particles of each type, all shards (signed; pushes add, claims subtract) [2]
   Ctl *phase;     // 0 source phase, 1 secondary phase
-  Ctl *cur_job;   // batch launches: per beam type (photon, electron), the first job
-                  // of that type that may still have histories to start [2]
+  Ctl *cur_job;   // batch launches: the first job that may still have histories to
+                  // start (word 0; word 1 unused)
   Ctl *job_next;  // batch launches: next history of each job [kMaxJobs]
   int refill_min;
   uint32_t guard[2];               // per-shard bound for sources, by beam type
@@ -325,8 +327,7 @@ __device__ __forceinline__ JobCtx job_ctx(const RunParams &R, int j) {
 // Start new source histories in the empty lanes: from the run's range, or
 // (batch) from the current job of the batch, job after job, so that one
 // job's phantom and tally are hot in L2 at a time.  A warp holding particles
-// of one type only starts histories of a job with that beam type (type < 0:
-// any job; the warp then takes the job's type).
+// of one type only starts histories of a job with that beam type.
 template <bool kMulti>
 __device__ int refill_source(const RunParams &R, const QDev &Q, unsigned empty, Part &p, bool &alive, QSink &sk,
                              int &type) {
