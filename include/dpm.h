@@ -90,9 +90,11 @@ typedef struct {
     int kernel;        /* DPM_KERNEL_QUEUE (persistent, particle queues) or
                           DPM_KERNEL_HISTORY (one history per thread, private stack) */
     int n_batches;     /* history batches for the sigma estimate (default 50, max 1024) */
-    int block_size;    /* threads per block (multiple of 32) */
-    int blocks_per_sm; /* resident blocks per SM for the persistent kernel */
-    int queue_log2;    /* log2 of each particle queue's capacity */
+    int block_size;    /* per-history kernel: threads per block (multiple of 32; 0 = 128).
+                          The queue kernel always runs blocks of 128 threads (it schedules
+                          per warp); its size is set by blocks_per_sm */
+    int blocks_per_sm; /* queue kernel: resident blocks per SM (0 = as many as fit, 8) */
+    int queue_log2;    /* queue kernel: log2 of each queue shard's capacity (7..20, 0 = 14) */
     int refill_min;    /* lanes that must be idle before a warp refills */
     double timeout_s;  /* bound on any device wait (default 20 s) */
     int physics_flags; /* DPM_NO_HARD: no Moller/bremsstrahlung events; DPM_NO_MSC: no

@@ -8,12 +8,23 @@ def test_coordinate_descent_finds_separable_optimum():
 
     def trial(o):
         calls.append(o)
-        return 1.0 + sum((o[k] - target[k]) ** 2 for k in target) * 0.01
+        return 1.0 + sum((o[k] - target[k]) ** 2 for k in target) * 0.1
 
     best, t, log = autotune.coordinate_descent(trial, autotune.DEFAULT_SPACE, autotune.DEFAULT_START)
     assert best == target
     assert t == 1.0
     assert len(calls) == len(log) < 4 * 3 * 3  # fewer trials than the full grid, none repeated
+
+
+def test_coordinate_descent_ignores_gains_below_the_noise_floor():
+    # every move gains 1 % at most: the start stays
+    def trial(o):
+        return 1.0 - 0.01 * (o["refill_min"] == 16) - 0.005 * (o["queue_log2"] == 15)
+
+    best, t, _ = autotune.coordinate_descent(trial, autotune.DEFAULT_SPACE, autotune.DEFAULT_START)
+    assert best == autotune.DEFAULT_START and t == 1.0
+    best, _, _ = autotune.coordinate_descent(trial, autotune.DEFAULT_SPACE, autotune.DEFAULT_START, min_gain=0.0)
+    assert best["refill_min"] == 16 and best["queue_log2"] == 15
 
 
 def test_cache_roundtrip(tmp_path):

@@ -112,3 +112,31 @@ def test_large_batch_with_phase_switches_equals_jobs_run_alone():
     assert st["error_flags"] == 0 and st["n_phase_switches"] >= 2
     for got, r in zip(raws, ref):
         assert np.array_equal(got, r)
+
+
+def test_autotuned_batch_keeps_the_tally(tmp_path):
+    """The autotuner times trial batches through the C ABI, resets the
+    tallies it touched and returns options from its search space; the batch
+    run with them reproduces the default launch's tally bit for bit."""
+    from paper_0910_0329_gb300 import autotune
+
+    spec = jobs_spec()[:3]
+    space = {"queue_log2": [12, 14], "blocks_per_sm": [6, 8], "refill_min": [8]}
+    with dpm.Dpm(0, W.MATERIALS, PARAMS) as d:
+        pids = [d.load_phantom(j[0]) for j in spec]
+        jobs = [(pid, src, first, n, seed) for pid, (_, src, first, n, seed) in zip(pids, spec)]
+        opts = autotune.tune_batch(d, jobs, "test-gpu", "three-jobs", fraction=0.5, space=space,
+                                   cache_path=str(tmp_path / "tune.json"))
+        assert all(opts[k] in v for k, v in space.items())
+        assert all(d.read(pid)[2].sum() == 0 for pid in pids)  # trial tallies were reset
+        assert autotune.load(autotune.signature("test-gpu", "three-jobs"), str(tmp_path / "tune.json"))["opts"] == opts
+        dpm.dpm_run_batch(d.ctx, jobs, dpm.run_opts(**opts))
+        dpm.dpm_batch_stats(d.ctx)
+        tuned = [d.read(pid)[2] for pid in pids]
+        for pid in pids:
+            dpm.dpm_reset_tally(d.ctx, pid)
+        dpm.dpm_run_batch(d.ctx, jobs, dpm.run_opts())
+        dpm.dpm_batch_stats(d.ctx)
+        plain = [d.read(pid)[2] for pid in pids]
+    for a, b in zip(tuned, plain):
+        assert np.array_equal(a, b)
