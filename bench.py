@@ -435,10 +435,10 @@ def bench_serve(args, rank, world, local):
     geoms = [W.blob_phantom(128, 128, 128, 0.3, 100 + k, name=f"patient{k}") for k in range(8)]
     ext = [g.extent for g in geoms]
 
-    def run(max_active):
+    def run(max_active, adaptive=True):
         reqs = serve.poisson_requests(args.requests, args.rate, 8, seed=5 + rank, geom_extent=ext)
         s = serve.Server(geoms, hbm_budget=48 << 30, chunk=args.chunk, target=0.01, max_active=max_active,
-                         device=local)
+                         device=local, adaptive=adaptive)
         warm = serve.poisson_requests(4, 1000.0, 8, seed=99, geom_extent=ext)
         s.run(warm)  # allocations and first launches
         s.stats = serve.ServeStats()
@@ -451,14 +451,17 @@ def bench_serve(args, rank, world, local):
 
     batched, clk = run(1024)
     plain, _ = run(1)
+    fixed, _ = run(1024, adaptive=False)
     line = {"metric": "histories/s", "value": batched["histories_per_s"] * world, "unit": "histories/s",
             "n_gpus": world, "steps": args.requests, "warmup": 4, "ms_per_step": 1000 * batched["wall_s"] / args.requests,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serve", "requests": args.requests, "rate_per_s": args.rate,
                        "geometries": "8 x 128^3 x 0.3 cm blob phantoms", "beamlet": "6 MV 0.5x0.5 cm, gantry U[0,360)",
-                       "target": "1 % sigma at D_max", "chunk": args.chunk, "parallelism": f"{world} replica(s)"},
+                       "target": "1 % sigma at D_max", "chunk": args.chunk,
+                       "rounds": "first round `chunk` histories, later rounds sized from the request's own sigma",
+                       "parallelism": f"{world} replica(s)"},
             "p50_latency_s": batched["p50_latency_s"], "p99_latency_s": batched["p99_latency_s"],
-            "served": batched, "single_request_path": plain, "clocks": clk}
+            "served": batched, "single_request_path": plain, "fixed_chunk_rounds": fixed, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

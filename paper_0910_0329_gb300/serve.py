@@ -10,8 +10,13 @@ request's D_max and its sigma (dpm_dmax_sigma) and retires the requests that
 reached the target relative uncertainty.  Requests that arrive meanwhile join
 at the next round, so work from different requests overlaps on the device.
 
-A request's k-th round always transports histories [k*chunk, (k+1)*chunk)
-with the request's own seed, and its stop decision looks only at its own
+A request's first round transports `chunk` histories.  With `adaptive`, each
+later round is sized from the request's own relative sigma at D_max: with r
+after n histories, about n*(r/target)^2 are needed in all, so the next round
+transports that (times `overshoot`, within [chunk, max_chunk]) minus n; most
+requests then finish in two rounds instead of n_final/chunk.  Without it every
+round transports `chunk`.  Round sizes, history ranges (consecutive, with the
+request's own seed) and the stop decision depend only on the request's own
 tally: its result is the same alone or in any mix.
 """
 from __future__ import annotations
@@ -37,6 +42,7 @@ class Request:
     done: float | None = None
     histories: int = 0
     rounds: int = 0
+    next_n: int = 0
     rel_sigma: float = math.inf
     dose_max: float = 0.0
     raw: np.ndarray | None = None
@@ -71,10 +77,14 @@ class ServeStats:
 
 class Server:
     def __init__(self, geometries, params=None, hbm_budget=16 << 30, chunk=200_000, target=0.01, n_batches=10,
-                 max_active=1024, keep_results=False, seed_base=10 ** 6, device=0, stream=None):
+                 max_active=1024, keep_results=False, seed_base=10 ** 6, device=0, stream=None, adaptive=True,
+                 max_chunk=None, overshoot=1.15):
         self.d = dpm.Dpm(device, W.MATERIALS, params or W.DEFAULT_PARAMS, stream=stream)
         self.geoms = list(geometries)
         self.chunk = int(chunk)
+        self.adaptive = bool(adaptive)
+        self.max_chunk = int(max_chunk) if max_chunk else 32 * self.chunk
+        self.overshoot = float(overshoot)
         self.target = float(target)
         self.n_batches = int(n_batches)
         self.max_active = int(max_active)
@@ -126,12 +136,13 @@ class Server:
                 continue
             r.slot = slot
             r.admitted = now
+            r.next_n = self.chunk
             self.active.append(r)
         self.pending = still
         self.stats.max_active = max(self.stats.max_active, len(self.active))
 
     def _round(self, clock):
-        jobs = [(r.slot, r.source, r.rounds * self.chunk, self.chunk, self.seed_base + r.rid) for r in self.active]
+        jobs = [(r.slot, r.source, r.histories, r.next_n, self.seed_base + r.rid) for r in self.active]
         dpm.dpm_run_batch(self.d.ctx, jobs, dpm.run_opts(n_batches=self.n_batches))
         res = dpm.dpm_dmax_sigma(self.d.ctx, [r.slot for r in self.active])
         now = clock()
@@ -139,10 +150,11 @@ class Server:
         keep = []
         for r, (dose, sig, vox) in zip(self.active, res):
             r.rounds += 1
-            r.histories += self.chunk
-            self.stats.histories += self.chunk
+            r.histories += r.next_n
+            self.stats.histories += r.next_n
             r.dose_max = dose
             r.rel_sigma = sig / dose if dose > 0 else math.inf
+            r.next_n = self._next_chunk(r)
             if r.rel_sigma <= self.target:
                 r.done = now
                 if self.keep:
@@ -153,6 +165,12 @@ class Server:
             else:
                 keep.append(r)
         self.active = keep
+
+    def _next_chunk(self, r):
+        if not self.adaptive or not math.isfinite(r.rel_sigma) or r.rel_sigma <= 0:
+            return self.chunk
+        need = r.histories * (r.rel_sigma / self.target) ** 2 * self.overshoot - r.histories
+        return int(min(max(need, self.chunk), self.max_chunk))
 
     def run(self, requests, clock=None, time_scale=1.0):
         """Serve `requests` (sorted by arrival, seconds from start) in real time
