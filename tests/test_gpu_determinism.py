@@ -96,11 +96,13 @@ def test_grid_phase_switches_do_not_change_the_tally(beam, queue_log2):
     assert np.array_equal(got, ref)
 
 
-def test_full_size_photon_launch_equals_history_kernel():
-    """The benchmarked configuration (6 MV, 10^7 histories in one launch with
-    the default queue): several phase switches, same tally as the
-    one-history-per-thread kernel."""
-    wl = W.c1_photon_wbw()
+@pytest.mark.parametrize("config", ["6mv", "blob128"])
+def test_full_size_launch_equals_history_kernel(config):
+    """The benchmarked configurations at full size (10^7 histories in one
+    launch with the default queue: 6 MV on the slab phantom, 20 MeV electrons
+    on the 128^3 blob phantom): phase switches happen, and the tally equals
+    the one-history-per-thread kernel's bit for bit."""
+    wl = W.c1_photon_wbw() if config == "6mv" else W.c2_electron_blob128()
     ref, _ = run_stats(wl, wl.n_histories, dpm.KERNEL_HISTORY)
     got, st = run_stats(wl, wl.n_histories, dpm.KERNEL_QUEUE)
     assert st["n_phase_switches"] >= 2
