@@ -437,8 +437,12 @@ __device__ DPM_COLD bool photon_interact(Part &p, const Ctx &R, Sink &s, EIdx e,
   return true;
 }
 
+// Woodcock flights until a real interaction.  With max_draws below the cap,
+// a call stops after that many random draws (two flights each) and returns
+// true with the photon in flight; the next call continues with the same
+// random numbers, so the photon's history does not depend on the split.
 template <class Ctx, class Sink>
-__device__ bool photon_segment(Part &p, const Ctx &R, Sink &s) {
+__device__ bool photon_segment(Part &p, const Ctx &R, Sink &s, int max_draws = kMaxPhotonFlights) {
   const DevTables &T = R.T;
   const DevPhantom &P = R.P;
   if (p.E <= T.eabs_g) {
@@ -449,7 +453,7 @@ __device__ bool photon_segment(Part &p, const Ctx &R, Sink &s) {
   const float mumax = lerp(__ldg(P.mu_max + e.i), __ldg(P.mu_max + e.i + 1), e.f);
   const float inv_mumax = 1.f / mumax;
   const float X = P.nx * P.dx, Y = P.ny * P.dy, Z = P.nz * P.dz;
-  for (int it = 0; it < kMaxPhotonFlights; ++it) {
+  for (int it = 0; it < max_draws; ++it) {
     const uint4 r = draw(p, R);
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -470,6 +474,7 @@ __device__ bool photon_segment(Part &p, const Ctx &R, Sink &s) {
       }
     }
   }
+  if (max_draws < kMaxPhotonFlights) return true;
   s.error(ERR_STEPCAP);
   s.deposit(vox(p, P), p.E);
   return false;

@@ -61,6 +61,11 @@ constexpr int kQBlock = 128;
 #define DPM_PHASE_GUARD_SHIFT_E 2
 #endif
 constexpr int kStealProbes = DPM_STEAL_PROBES;
+// Random draws (two Woodcock flights each) a photon lane makes per warp step:
+// a warp does not wait for its lane with the longest run of virtual flights.
+#ifndef DPM_PHOTON_DRAWS
+#define DPM_PHOTON_DRAWS 1
+#endif
 constexpr int kSpillProbes = 8;
 
 struct alignas(128) Ctl {
@@ -564,8 +569,9 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
     }
     if (alive) {
       if (mode == 0) {
-        alive = kMulti ? photon_segment(p, job_ctx(R, p.job), sk) : photon_segment(p, R, sk);
-        if (alive && ++nstep >= kMaxPhotonSegments) {
+        alive = kMulti ? photon_segment(p, job_ctx(R, p.job), sk, DPM_PHOTON_DRAWS)
+                       : photon_segment(p, R, sk, DPM_PHOTON_DRAWS);
+        if (alive && ++nstep >= kMaxPhotonSegments * 8) {
           sk.error(ERR_STEPCAP);
           sk.deposit(kMulti ? vox(p, R.jobs[p.job].P) : vox(p, R.P), p.E);
           alive = false;
