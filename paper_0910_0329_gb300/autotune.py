@@ -16,9 +16,9 @@ import os
 DEFAULT_SPACE = {
     "queue_log2": [12, 13, 14, 15],
     "blocks_per_sm": [4, 6, 8],
-    "refill_min": [4, 8, 16],
+    "refill_min": [0, 8, 16, 24],  # 0: the library's per-type defaults (20 photon, 12 electron lanes)
 }
-DEFAULT_START = {"queue_log2": 14, "blocks_per_sm": 8, "refill_min": 8}
+DEFAULT_START = {"queue_log2": 14, "blocks_per_sm": 8, "refill_min": 0}
 
 
 def coordinate_descent(trial, space=None, start=None, passes=2, min_gain=0.02):
