@@ -117,7 +117,9 @@ typedef struct {
     uint64_t n_tally_atomics;     /* 64-bit atomic adds issued to the tally */
     uint64_t n_pushed;            /* secondaries created */
     double transport_ms;          /* device time of the transport kernels of the runs read
-                                     (CUDA events recorded around each launch on its stream) */
+                                     (CUDA events recorded around each launch on its stream; a
+                                     phantom keeps the events of at most 1024 unread runs, the
+                                     times of older ones are summed early, waiting for them) */
     double fold_ms;               /* device time of the batch folds of those runs */
     uint64_t n_transport_launches;/* transport kernel launches since the previous read */
     uint64_t n_phase_switches;    /* queue kernel: grid-wide switches between the source phase and

@@ -170,6 +170,19 @@ extern "C" int dpm_run_batch(dpm_ctx *c, const dpm_job *jobs, int n_jobs, const 
   R.counters = c->d_batch_counters;
   R.err = c->d_err;
 
+  if (c->batch_ev.size() + 2 > kMaxPendingEvents) {
+    // retire the older half of the pending start/end pairs into host sums
+    const size_t n = (c->batch_ev.size() / 4) * 2;
+    cudaEventSynchronize(c->batch_ev[n - 1]);
+    for (size_t i = 0; i + 1 < n; i += 2) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, c->batch_ev[i], c->batch_ev[i + 1]) == cudaSuccess) c->batch_folded_ms += ms;
+      c->batch_folded_launches++;
+    }
+    for (size_t i = 0; i < n; ++i) cudaEventDestroy(c->batch_ev[i]);
+    c->batch_ev.erase(c->batch_ev.begin(), c->batch_ev.begin() + long(n));
+    cudaGetLastError();
+  }
   cudaEvent_t ev[2];
   for (int i = 0; i < 2; ++i) BATCH_TRY(c, cudaEventCreate(&ev[i]));
   c->batch_ev.push_back(ev[0]);
@@ -260,6 +273,10 @@ extern "C" int dpm_batch_stats(dpm_ctx *c, dpm_run_stats *st) {
     st->n_pushed = cnt[C_PUSH];
     st->n_phase_switches = cnt[C_SWITCH];
   }
+  st->transport_ms = c->batch_folded_ms;
+  st->n_transport_launches = c->batch_folded_launches;
+  c->batch_folded_ms = 0;
+  c->batch_folded_launches = 0;
   for (size_t i = 0; i + 1 < c->batch_ev.size(); i += 2) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, c->batch_ev[i], c->batch_ev[i + 1]) == cudaSuccess) st->transport_ms += ms;

@@ -26,6 +26,25 @@ namespace {
 void drop_events(PhantomState *p) {
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   p->ev.clear();
+  p->folded_transport_ms = p->folded_fold_ms = 0;
+  p->folded_launches = 0;
+}
+
+// Retire the older half of a phantom's run events into host sums (waits for
+// those runs only).
+void fold_old_events(PhantomState *p) {
+  const size_t n = (p->ev.size() / 6) * 3;
+  if (n == 0) return;
+  cudaEventSynchronize(p->ev[n - 1]);
+  for (size_t i = 0; i + 2 < n; i += 3) {
+    float a = 0, b = 0;
+    if (cudaEventElapsedTime(&a, p->ev[i], p->ev[i + 1]) == cudaSuccess) p->folded_transport_ms += a;
+    if (cudaEventElapsedTime(&b, p->ev[i + 1], p->ev[i + 2]) == cudaSuccess) p->folded_fold_ms += b;
+    p->folded_launches++;
+  }
+  for (size_t i = 0; i < n; ++i) cudaEventDestroy(p->ev[i]);
+  p->ev.erase(p->ev.begin(), p->ev.begin() + long(n));
+  cudaGetLastError();
 }
 
 int fail(dpm_ctx *c, int code, const std::string &msg) {
@@ -382,6 +401,7 @@ int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t 
 
   cudaEvent_t ev[3];
   for (int i = 0; i < 3; ++i) CUDA_TRY(c, cudaEventCreate(&ev[i]));
+  if (p->ev.size() + 3 > kMaxPendingEvents) fold_old_events(p);
   for (int i = 0; i < 3; ++i) p->ev.push_back(ev[i]);
   if (o.kernel == DPM_KERNEL_HISTORY) {
     CUDA_TRY(c, cudaEventRecord(ev[0], c->stream));
@@ -468,6 +488,9 @@ static int read_common(dpm_ctx *c, PhantomState *p, const int64_t *s1_host, dpm_
     st->n_tally_atomics = cnt[C_ATOM];
     st->n_pushed = cnt[C_PUSH];
     st->n_phase_switches = cnt[C_SWITCH];
+    st->transport_ms = p->folded_transport_ms;
+    st->fold_ms = p->folded_fold_ms;
+    st->n_transport_launches = p->folded_launches;
     for (size_t i = 0; i + 2 < p->ev.size(); i += 3) {
       float a = 0, b = 0;
       if (cudaEventElapsedTime(&a, p->ev[i], p->ev[i + 1]) == cudaSuccess) st->transport_ms += a;

@@ -15,6 +15,12 @@ namespace dpm {
 
 constexpr int kMaxTableNodes = 65536;  // upper bound of dpm_table_params.n_e
 
+// Timing events kept per phantom (and per context for batches) between two
+// reads of the statistics; past this many the oldest half is waited for,
+// its times are summed on the host and its events are released, so that a
+// caller that never reads the statistics holds a bounded number of events.
+constexpr size_t kMaxPendingEvents = 3 * 1024;
+
 struct PhantomState {
   int nx = 0, ny = 0, nz = 0;
   double dx = 0, dy = 0, dz = 0;
@@ -35,8 +41,11 @@ struct PhantomState {
   unsigned long long *d_dmax = nullptr;  // [1] key + [3] doubles for the D_max query
   uint64_t n_total = 0;
   uint64_t b_total = 0;
-  // CUDA events around each transport launch and fold since the last read
+  // CUDA events around each transport launch and fold since the last read;
+  // beyond kMaxPendingEvents the oldest runs' times move to the sums below
   std::vector<cudaEvent_t> ev;
+  double folded_transport_ms = 0, folded_fold_ms = 0;
+  uint64_t folded_launches = 0;
 };
 
 }  // namespace dpm
@@ -59,6 +68,8 @@ struct dpm_ctx {
   dpm::DevJob *d_jobs = nullptr;               // job table, kMaxJobs entries
   unsigned long long *d_batch_counters = nullptr;  // [kCounterSlots]
   std::vector<cudaEvent_t> batch_ev;           // start/end pairs since the last dpm_batch_stats
+  double batch_folded_ms = 0;                  // times of pairs retired early (see kMaxPendingEvents)
+  uint64_t batch_folded_launches = 0;
   uint64_t batch_histories = 0;
   cudaGraphExec_t batch_exec = nullptr;
   std::vector<uint64_t> batch_sig;             // shape the cached graph was captured for

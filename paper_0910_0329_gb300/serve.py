@@ -61,6 +61,7 @@ class ServeStats:
     wall: float = 0.0
     max_active: int = 0
     peak_bytes: int = 0
+    gpu_ms: float = 0.0
 
     def latencies(self):
         return np.array([r.latency for r in self.completed])
@@ -72,7 +73,8 @@ class ServeStats:
                 "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
                 "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
                 "mean_histories_per_request": self.histories / max(len(self.completed), 1),
-                "max_active": self.max_active, "peak_slot_bytes": self.peak_bytes}
+                "max_active": self.max_active, "peak_slot_bytes": self.peak_bytes,
+                "gpu_busy_frac": self.gpu_ms / 1000.0 / self.wall if self.wall else 0.0}
 
 
 class Server:
@@ -145,6 +147,10 @@ class Server:
         jobs = [(r.slot, r.source, r.histories, r.next_n, self.seed_base + r.rid) for r in self.active]
         dpm.dpm_run_batch(self.d.ctx, jobs, dpm.run_opts(n_batches=self.n_batches))
         res = dpm.dpm_dmax_sigma(self.d.ctx, [r.slot for r in self.active])
+        # the round's device status (raises on a queue overflow or a timed-out
+        # wait) and release of its timing events
+        st = dpm.dpm_batch_stats(self.d.ctx)
+        self.stats.gpu_ms += st["transport_ms"]
         now = clock()
         self.stats.rounds += 1
         keep = []

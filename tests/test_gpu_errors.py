@@ -80,3 +80,22 @@ def test_wait_timeout_is_reported_and_recoverable():
         d.run(pid, wl.source, 5000, wl.seed, kernel=dpm.KERNEL_QUEUE)
         raw = d.read(pid)[2]
     assert np.array_equal(raw, _ref_tally(wl, 5000))
+
+
+def test_timing_events_stay_bounded_without_reads():
+    """Runs that are never read keep at most a bounded number of timing
+    events; the statistics of the next read still cover every run."""
+    wl = W.c1_photon_wbw()
+    with dpm.Dpm(0, W.MATERIALS, wl.params) as d:
+        pid = d.load_phantom(wl.phantom)
+        for i in range(1100):
+            d.run(pid, wl.source, 20, wl.seed, first=20 * i)
+        _, _, raw, st = d.read(pid)
+        assert st["n_histories"] == 22000 and st["n_transport_launches"] == 1100
+        assert st["transport_ms"] > 0 and st["error_flags"] == 0
+        jobs = [(pid, wl.source, 0, 20, 1)]
+        for i in range(1100):
+            dpm.dpm_run_batch(d.ctx, jobs, dpm.run_opts())
+        bst = dpm.dpm_batch_stats(d.ctx)
+        assert bst["n_transport_launches"] == 1100 and bst["transport_ms"] > 0
+        assert bst["n_histories"] == 22000
