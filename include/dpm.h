@@ -21,6 +21,8 @@
  *   - work is queued on the context's stream (dpm_set_stream, default: a
  *     stream the context creates); dpm_run() is asynchronous, dpm_read_dose()
  *     and dpm_sync() synchronise and report device-side errors;
+ *   - a context is used by one host thread at a time (contexts on different
+ *     threads, or different devices, are independent);
  *   - phantom layout: voxel v = i + nx*(j + ny*k); the phantom occupies
  *     [0,nx*dx] x [0,ny*dy] x [0,nz*dz] cm; mat[v] indexes the material list
  *     given to dpm_build_tables(); rho[v] is the mass density in g/cm^3.
@@ -131,7 +133,8 @@ void dpm_destroy(dpm_ctx *ctx);
 const char *dpm_last_error(const dpm_ctx *ctx);
 
 /* Use an external CUDA stream (cudaStream_t passed as void*); NULL restores
-   the context's own stream. */
+   the context's own stream.  Waits for the work queued on the previous stream
+   first, so that no run of the context overlaps another. */
 int dpm_set_stream(dpm_ctx *ctx, void *cuda_stream);
 
 /* Copy a voxel phantom (host arrays, nx*ny*nz entries) to the device.  Sizes

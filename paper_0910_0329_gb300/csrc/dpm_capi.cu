@@ -259,6 +259,10 @@ const char *dpm_last_error(const dpm_ctx *c) { return c ? c->err.c_str() : "null
 
 int dpm_set_stream(dpm_ctx *c, void *s) {
   if (!c) return DPM_EINVAL;
+  cudaSetDevice(c->device);
+  // the queues, counters and error word are shared by all runs of the context
+  const cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, DPM_ECUDA, std::string("previous stream: ") + cudaGetErrorString(e));
   c->stream = s ? (cudaStream_t)s : c->own;
   return DPM_OK;
 }
