@@ -27,7 +27,9 @@ def coordinate_descent(trial, space=None, start=None, passes=2, min_gain=0.02):
     noise does not pull the choice away from the start); returns (best_opts,
     best_time, log of (opts, time))."""
     space = space or DEFAULT_SPACE
-    best = dict(start or {k: v[len(v) // 2] for k, v in space.items()})
+    start = start or {}
+    # start from `start` where it lies in the space, else from the middle value
+    best = {k: start[k] if start.get(k) in v else v[len(v) // 2] for k, v in space.items()}
     seen = {}
 
     def cost(opts):

@@ -120,6 +120,18 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
 
 __device__ __forceinline__ uint32_t ld_volatile32(const uint32_t *p) { return *(const volatile uint32_t *)p; }
 
+// Slot sequence words: the producer publishes a record and the consumer
+// frees its slot with a release store; both wait for the word with acquire
+// loads, so the record's plain loads and stores are ordered around them.
+__device__ __forceinline__ uint32_t ld_acquire32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release32(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
 // Occupancy of a shard from two relaxed loads.  The loads of head and tail
 // may be observed in either order, so a concurrent consumer can make head
 // appear ahead of tail: the difference saturates at zero.
@@ -220,9 +232,9 @@ struct QSink {
     const uint32_t slot = uint32_t(p) & Q.mask;
     const size_t idx = (size_t(shard) << Q.log2cs) + slot;
     // wait for the consumer of position p - capacity to have freed the slot
-    if (ld_volatile32(Qt.seq + idx) != uint32_t(p)) {
+    if (ld_acquire32(Qt.seq + idx) != uint32_t(p)) {
       const unsigned long long t0 = now_ns();
-      while (ld_volatile32(Qt.seq + idx) != uint32_t(p)) {
+      while (ld_acquire32(Qt.seq + idx) != uint32_t(p)) {
         if (now_ns() - t0 > Q.timeout_ns) {
           err |= ERR_TIMEOUT;
           return;
@@ -242,8 +254,7 @@ struct QSink {
     Qt.idh[idx] = q.id_hi;
     Qt.hist[idx] = q.hist | (q.type == POSITRON ? 0x80000000u : 0u);
     Qt.job[idx] = uint32_t(q.job);
-    __threadfence();
-    *(volatile uint32_t *)(Qt.seq + idx) = uint32_t(p + 1);
+    st_release32(Qt.seq + idx, uint32_t(p + 1));
   }
 };
 
@@ -276,9 +287,9 @@ __device__ __forceinline__ bool take(const QDev &Q, int t, int s, unsigned long 
   const QType &Qt = Q.q[t];
   const uint32_t slot = uint32_t(p) & Q.mask;
   const size_t idx = (size_t(s) << Q.log2cs) + slot;
-  if (ld_volatile32(Qt.seq + idx) != uint32_t(p + 1)) {
+  if (ld_acquire32(Qt.seq + idx) != uint32_t(p + 1)) {
     const unsigned long long t0 = now_ns();
-    while (ld_volatile32(Qt.seq + idx) != uint32_t(p + 1)) {
+    while (ld_acquire32(Qt.seq + idx) != uint32_t(p + 1)) {
       if (now_ns() - t0 > Q.timeout_ns) {
         err |= ERR_TIMEOUT;
         return false;
@@ -286,7 +297,6 @@ __device__ __forceinline__ bool take(const QDev &Q, int t, int s, unsigned long 
       __nanosleep(32);
     }
   }
-  __threadfence();
   o.x = __ldcg(Qt.x + idx);
   o.y = __ldcg(Qt.y + idx);
   o.z = __ldcg(Qt.z + idx);
@@ -305,8 +315,7 @@ __device__ __forceinline__ bool take(const QDev &Q, int t, int s, unsigned long 
   o.type = t == 0 ? PHOTON : ((h >> 31) ? POSITRON : ELECTRON);
   o.job = int(__ldcg(Qt.job + idx));
   o.ctr = 0;
-  __threadfence();
-  *(volatile uint32_t *)(Qt.seq + idx) = uint32_t(p + (1ull << Q.log2cs));
+  st_release32(Qt.seq + idx, uint32_t(p + (1ull << Q.log2cs)));
   return true;
 }
 

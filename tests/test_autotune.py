@@ -27,6 +27,13 @@ def test_coordinate_descent_ignores_gains_below_the_noise_floor():
     assert best["refill_min"] == 16 and best["queue_log2"] == 15
 
 
+def test_start_outside_the_space_is_projected():
+    space = {"queue_log2": [12, 14], "blocks_per_sm": [6, 8], "refill_min": [8]}
+    best, _, log = autotune.coordinate_descent(lambda o: 1.0, space, autotune.DEFAULT_START)
+    assert best == {"queue_log2": 14, "blocks_per_sm": 8, "refill_min": 8}
+    assert all(all(o[k] in space[k] for k in space) for o, _ in log)
+
+
 def test_cache_roundtrip(tmp_path):
     p = str(tmp_path / "t.json")
     k = autotune.signature("GB300", "batch64")
