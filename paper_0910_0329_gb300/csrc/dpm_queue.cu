@@ -418,7 +418,20 @@ __device__ bool any_work(const RunParams &R, const QDev &Q) {
   return __any_sync(kFull, w);
 }
 
-// False while either of the CTA's shards is above its high-water mark.
+// Cheap version of any_work() from the global per-type backlog counters
+// (exact once the pushes and claims in flight have landed; used to decide
+// whether an idle warp should retry, never to end the run).
+template <bool kMulti>
+__device__ bool any_work_hint(const RunParams &R, const QDev &Q) {
+  bool w = false;
+  if ((threadIdx.x & 31) == 0) {
+    w = (long long)ld_volatile(&Q.backlog[0].v) > 0 || (long long)ld_volatile(&Q.backlog[1].v) > 0;
+    if (!kMulti && ld_volatile(&Q.next_hist->v) < R.n) w = true;
+    if (kMulti && ld_volatile(&Q.cur_job[0].v) < (unsigned long long)R.n_jobs) w = true;
+  }
+  return __shfl_sync(kFull, w, 0);
+}
+
 // True while both of the CTA's shards hold at most `bound` particles (warp-uniform).
 __device__ bool source_allowed(const QDev &Q, int home, unsigned long long bound) {
   bool ok = true;
@@ -504,6 +517,7 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
   bool idle = false;
   unsigned long long idle_t0 = 0;
   unsigned sleep_ns = 128;
+  unsigned retry_ns = 32;
   const unsigned long long t_start = __shfl_sync(kFull, now_ns(), 0);
   for (;;) {
     unsigned live = __ballot_sync(kFull, alive);
@@ -551,6 +565,10 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
         nstep = 0;
       }
       live = __ballot_sync(kFull, alive);
+      if (live != 0u) {
+        retry_ns = 32;
+        sleep_ns = 128;
+      }
     }
     if (live == 0) {
       // nothing in the lanes: idle until work appears or the run is over
@@ -560,14 +578,17 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
         idle = true;
         idle_t0 = now_ns();
       }
-      if (any_work<kMulti>(R, Q)) {
+      if (any_work_hint<kMulti>(R, Q)) {
+        // work exists but this warp found none within reach: retry after a
+        // short, growing pause instead of rescanning at once
         if (lane == 0) atomicAdd(&Q.idle->v, ~0ull);  // -1
         idle = false;
-        sleep_ns = 128;
         if (__shfl_sync(kFull, now_ns() - t_start > Q.deadline_ns, 0)) {
           sk.error(ERR_TIMEOUT);
           break;
         }
+        __nanosleep(retry_ns);
+        retry_ns = min(retry_ns * 2, 2048u);
         continue;
       }
       bool done = false;
