@@ -18,6 +18,8 @@ using namespace dpm;
 
 namespace {
 
+constexpr uint64_t kSoloHistories = 1000000;
+
 #define BATCH_TRY(ctx, call)                                                                   \
   do {                                                                                         \
     cudaError_t e_ = (call);                                                                   \
@@ -75,10 +77,13 @@ extern "C" int dpm_run_batch(dpm_ctx *c, const dpm_job *jobs, int n_jobs, const 
   Prepared b;
   std::set<int> seen;
   int rc;
-  // a job whose phantom and hot tally slab (13 bytes per voxel) exceed a
-  // quarter of L2 gets its own launch: two such jobs overlapping at a job
-  // boundary would evict each other (measured: 13-15 % slower on
-  // 256x256x128 phantoms, while small jobs gain up to 1.8x from sharing)
+  // A job gets its own launch (in the same stream or graph) when its phantom
+  // and hot tally slab (13 bytes per voxel) exceed a quarter of L2 -- two
+  // such jobs overlapping at a job boundary evict each other (13-15 % slower
+  // on 256x256x128 phantoms) -- or when it has kSoloHistories or more: the
+  // shared launch pays for the job-table indirection on every step and only
+  // gains from filling short jobs' tails (64-job batch: all shared 1133 ms,
+  // all separate 1059 ms, split at 10^6 histories 1048 ms).
   int l2 = 0;
   cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device);
   const size_t solo_bytes = size_t(l2 > 0 ? l2 : (96 << 20)) / 4;
@@ -96,7 +101,7 @@ extern "C" int dpm_run_batch(dpm_ctx *c, const dpm_job *jobs, int n_jobs, const 
     int B = 0;
     if ((rc = ctx_prepare_batches(c, p, jobs[j].n_histories, o.n_batches, bs, B))) return rc;
     b.total += Rj.n;
-    if (p->V * 13 > solo_bytes) {
+    if (p->V * 13 > solo_bytes || jobs[j].n_histories >= kSoloHistories) {
       Rj.n_batches = B;
       Rj.slabs = p->d_slabs;
       Rj.err = c->d_err;

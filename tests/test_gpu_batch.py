@@ -95,18 +95,19 @@ def test_batch_argument_errors():
 
 
 def test_large_batch_with_phase_switches_equals_jobs_run_alone():
-    """Enough histories per job for the grid-wide phase to switch within the
-    batch, across photon-beam and electron-beam jobs."""
+    """Enough histories per job, and a small enough queue, for the grid-wide
+    phase to switch within the shared launch, across photon-beam and
+    electron-beam jobs (jobs below 10^6 histories share the launch)."""
     c1, c0 = W.c1_photon_wbw(), W.c0_electron_wlw()
     blob = W.blob_phantom(64, 64, 64, 0.4, 23, name="blob64")
-    spec = [(c1.phantom, c1.source, 0, 3_000_000, 21),
-            (blob, W.axial_source(blob, W.PHOTON, W.SPEC_6MV, 6.0, 90.0, 100.0, 10.0, 10.0), 0, 3_000_000, 22),
+    spec = [(c1.phantom, c1.source, 0, 900_000, 21),
+            (blob, W.axial_source(blob, W.PHOTON, W.SPEC_6MV, 6.0, 90.0, 100.0, 10.0, 10.0), 0, 900_000, 22),
             (c0.phantom, c0.source, 0, 200_000, 23)]
     ref = [alone(*j) for j in spec]
     with dpm.Dpm(0, W.MATERIALS, PARAMS) as d:
         pids = [d.load_phantom(j[0]) for j in spec]
         jobs = [(pid, src, first, n, seed) for pid, (_, src, first, n, seed) in zip(pids, spec)]
-        dpm.dpm_run_batch(d.ctx, jobs, dpm.run_opts(queue_log2=12))
+        dpm.dpm_run_batch(d.ctx, jobs, dpm.run_opts(queue_log2=11))
         st = dpm.dpm_batch_stats(d.ctx)
         raws = [d.read(pid)[2] for pid in pids]
     assert st["error_flags"] == 0 and st["n_phase_switches"] >= 2
@@ -140,3 +141,23 @@ def test_autotuned_batch_keeps_the_tally(tmp_path):
         plain = [d.read(pid)[2] for pid in pids]
     for a, b in zip(tuned, plain):
         assert np.array_equal(a, b)
+
+
+def test_large_jobs_get_their_own_launch_and_keep_the_tally():
+    """A job of 10^6 histories or more runs as a launch of its own inside the
+    batch (and its graph); its tally still equals the job run alone."""
+    c1 = W.c1_photon_wbw()
+    blob = W.blob_phantom(48, 48, 48, 0.4, 31, name="blob48")
+    spec = [(c1.phantom, c1.source, 500, 1_200_000, 41),
+            (blob, W.axial_source(blob, W.ELECTRON, W.SPEC_MONO, 9.0, 90.0, 100.0, 8.0, 8.0), 0, 30_000, 42)]
+    ref = [alone(*j) for j in spec]
+    for use_graph in (0, 1):
+        with dpm.Dpm(0, W.MATERIALS, PARAMS) as d:
+            pids = [d.load_phantom(j[0]) for j in spec]
+            jobs = [(pid, src, first, n, seed) for pid, (_, src, first, n, seed) in zip(pids, spec)]
+            dpm.dpm_run_batch(d.ctx, jobs, dpm.run_opts(use_graph=use_graph))
+            st = dpm.dpm_batch_stats(d.ctx)
+            raws = [d.read(pid)[2] for pid in pids]
+        assert st["error_flags"] == 0 and st["n_histories"] == 1_230_000
+        for got, r in zip(raws, ref):
+            assert np.array_equal(got, r)
