@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--autotune", action="store_true", help="tune the batched launch before timing it")
     ap.add_argument("--requests", type=int, default=500, help="requests of the serve workload")
     ap.add_argument("--rate", type=float, default=20.0, help="request arrival rate of the serve workload (1/s)")
-    ap.add_argument("--chunk", type=int, default=200000, help="histories per request and round (serve)")
+    ap.add_argument("--chunk", type=int, default=200000, help="histories of a request's first round (serve)")
+    ap.add_argument("--round-budget", type=int, default=0, help="histories per serving round (0: the server's default)")
     return ap.parse_args()
 
 
@@ -438,7 +439,7 @@ def bench_serve(args, rank, world, local):
     def run(max_active, adaptive=True):
         reqs = serve.poisson_requests(args.requests, args.rate, 8, seed=5 + rank, geom_extent=ext)
         s = serve.Server(geoms, hbm_budget=48 << 30, chunk=args.chunk, target=0.01, max_active=max_active,
-                         device=local, adaptive=adaptive)
+                         device=local, adaptive=adaptive, round_budget=args.round_budget or None)
         warm = serve.poisson_requests(4, 1000.0, 8, seed=99, geom_extent=ext)
         s.run(warm)  # allocations and first launches
         s.stats = serve.ServeStats()

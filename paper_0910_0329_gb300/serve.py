@@ -18,6 +18,13 @@ requests then finish in two rounds instead of n_final/chunk.  Without it every
 round transports `chunk`.  Round sizes, history ranges (consecutive, with the
 request's own seed) and the stop decision depend only on the request's own
 tally: its result is the same alone or in any mix.
+
+A round takes the active requests oldest first until their next chunks reach
+`round_budget` histories (at least one request).  Under load this keeps the
+server close to first-come-first-served -- which minimises the mean latency
+of similar requests -- while younger requests fill the round's tail, instead
+of advancing every active request together (processor sharing, whose rounds
+and latencies grow with the queue).
 """
 from __future__ import annotations
 
@@ -80,13 +87,14 @@ class ServeStats:
 class Server:
     def __init__(self, geometries, params=None, hbm_budget=16 << 30, chunk=200_000, target=0.01, n_batches=10,
                  max_active=1024, keep_results=False, seed_base=10 ** 6, device=0, stream=None, adaptive=True,
-                 max_chunk=None, overshoot=1.15):
+                 max_chunk=None, overshoot=1.15, round_budget=None):
         self.d = dpm.Dpm(device, W.MATERIALS, params or W.DEFAULT_PARAMS, stream=stream)
         self.geoms = list(geometries)
         self.chunk = int(chunk)
         self.adaptive = bool(adaptive)
         self.max_chunk = int(max_chunk) if max_chunk else 32 * self.chunk
         self.overshoot = float(overshoot)
+        self.round_budget = int(round_budget) if round_budget else 40 * self.chunk
         self.target = float(target)
         self.n_batches = int(n_batches)
         self.max_active = int(max_active)
@@ -144,17 +152,18 @@ class Server:
         self.stats.max_active = max(self.stats.max_active, len(self.active))
 
     def _round(self, clock):
-        jobs = [(r.slot, r.source, r.histories, r.next_n, self.seed_base + r.rid) for r in self.active]
+        chosen = select_round(self.active, self.round_budget)
+        jobs = [(r.slot, r.source, r.histories, r.next_n, self.seed_base + r.rid) for r in chosen]
         dpm.dpm_run_batch(self.d.ctx, jobs, dpm.run_opts(n_batches=self.n_batches))
-        res = dpm.dpm_dmax_sigma(self.d.ctx, [r.slot for r in self.active])
+        res = dpm.dpm_dmax_sigma(self.d.ctx, [r.slot for r in chosen])
         # the round's device status (raises on a queue overflow or a timed-out
         # wait) and release of its timing events
         st = dpm.dpm_batch_stats(self.d.ctx)
         self.stats.gpu_ms += st["transport_ms"]
         now = clock()
         self.stats.rounds += 1
-        keep = []
-        for r, (dose, sig, vox) in zip(self.active, res):
+        done_ids = set()
+        for r, (dose, sig, vox) in zip(chosen, res):
             r.rounds += 1
             r.histories += r.next_n
             self.stats.histories += r.next_n
@@ -168,9 +177,8 @@ class Server:
                 self._release(r.slot)
                 r.slot = None
                 self.stats.completed.append(r)
-            else:
-                keep.append(r)
-        self.active = keep
+                done_ids.add(r.rid)
+        self.active = [r for r in self.active if r.rid not in done_ids]
 
     def _next_chunk(self, r):
         if not self.adaptive or not math.isfinite(r.rel_sigma) or r.rel_sigma <= 0:
@@ -202,6 +210,20 @@ class Server:
 
     def close(self):
         self.d.close()
+
+
+def select_round(active, budget):
+    """The requests of the next round: oldest first (`active` is in arrival
+    order), each with its whole next chunk, while the chunks fit in `budget`
+    histories; a request that does not fit is passed over for younger ones
+    with smaller chunks.  The oldest request always runs."""
+    chosen, total = [], 0
+    for r in active:
+        if chosen and total + r.next_n > budget:
+            continue
+        chosen.append(r)
+        total += r.next_n
+    return chosen
 
 
 def poisson_requests(n, rate, n_geoms, seed=5, beamlet=0.5, geom_extent=None):

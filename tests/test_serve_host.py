@@ -41,3 +41,12 @@ def test_poisson_requests_are_seeded_and_ordered():
     assert {r.geometry for r in a} == {0, 1, 2}
     # mean inter-arrival time near 1/rate
     assert abs(a[-1].arrival / 50 - 1 / 20.0) < 0.5 / 20.0
+
+
+def test_rounds_take_the_oldest_requests_within_the_budget():
+    reqs = [serve.Request(i, 0, None, float(i), next_n=n) for i, n in enumerate([5000, 4000, 200, 3000, 200])]
+    # 5000 + 200 + 200 fit in 6000; 4000 and 3000 wait
+    assert [r.rid for r in serve.select_round(reqs, 6000)] == [0, 2, 4]
+    # the oldest runs even alone above the budget
+    assert [r.rid for r in serve.select_round(reqs, 100)] == [0]
+    assert [r.rid for r in serve.select_round(reqs, 10 ** 9)] == [0, 1, 2, 3, 4]
