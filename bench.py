@@ -127,6 +127,18 @@ def profiled_traffic(kernel: str, workload: str, key: str = "traffic_bytes_per_h
     return float(tb.group(1)) if kernel_fingerprint() == fp.group(1) else None
 
 
+def deposit_stream(raw, n, seed=0):
+    """n voxel ids drawn independently with probability proportional to the
+    integer tally `raw`: a proxy for how often each voxel receives a deposit
+    (the hot spots of the dose are the hot spots of the tally atomics)."""
+    import numpy as np
+
+    w = np.clip(np.asarray(raw, np.float64), 0, None)
+    cdf = np.cumsum(w)
+    u = np.random.default_rng(seed).random(n) * cdf[-1]
+    return np.minimum(np.searchsorted(cdf, u, side="right"), len(w) - 1).astype(np.uint32)
+
+
 def kernel_fingerprint():
     """First 16 hex digits of the sha256 of the transport kernel's sources
     (dpm_device.cuh, dpm_queue.cu, dpm_internal.h) with comments and
@@ -322,11 +334,18 @@ def main():
     # L2 ceilings measured now by dpm_diag_l2_peaks
     atom_pk, l2_pk = dpm.dpm_diag_l2_peaks(d.ctx, 16 << 20)
     atom_rate = atom_per_hist * hist_per_launch / t_kernel_s
+    # the tally's own address stream: ids drawn from this run's tally, replayed
+    # as 64-bit atomic adds at full occupancy (hot-spot contention included)
+    replay_pk = dpm.dpm_diag_atomic_replay(d.ctx, deposit_stream(raw, 1 << 24), ph.n_vox)
     l2_bph = profiled_traffic(kname, args.workload, "l2_bytes_per_history")
     l2_rate = l2_bph * hist_per_launch / t_kernel_s if l2_bph else None
     line["l2_roofline"] = {
         "atomics": {"achieved": atom_rate, "peak": atom_pk, "unit": "atomics/s", "frac": atom_rate / atom_pk,
                     "what": "tally atomics of the transport kernel vs scattered 64-bit atomics over 16 MiB"},
+        "atomics_replay": {"achieved": atom_rate, "peak": replay_pk, "unit": "atomics/s",
+                           "frac": atom_rate / replay_pk,
+                           "what": "tally atomics vs the same phantom's deposit address distribution (2^24 ids "
+                                   "drawn from this run's tally) replayed as 64-bit atomic adds"},
         "bandwidth": {"achieved": l2_rate / 1e9 if l2_rate else None, "peak": l2_pk / 1e9, "unit": "GB/s",
                       "frac": l2_rate / l2_pk if l2_rate else None, "bytes_per_history": l2_bph,
                       "what": "L1->L2 sectors per history (ncu capture of this kernel) vs L1-bypassing loads "

@@ -235,6 +235,15 @@ int dpm_diag_philox(dpm_ctx *ctx, int n, const uint32_t *ctr, const uint32_t *ke
    Synchronous.  DPM_EINVAL for a bad size or a null out (host, 2 doubles). */
 int dpm_diag_l2_peaks(dpm_ctx *ctx, uint64_t ws_bytes, double *out);
 
+/* The atomic ceiling of the voxel tally for a given deposit address stream
+   (not a step of the paper's method): ids[0..n) (host; voxel indices below
+   n_vox, n <= 2^28) are issued as 64-bit atomic adds into a zeroed slab of
+   n_vox counters by a grid of 8 blocks of 256 threads per SM, once to warm
+   L2 and once timed.  *rate receives adds per second.  The call allocates
+   and frees its device buffers and is synchronous.  DPM_EINVAL for bad
+   sizes or an id out of range. */
+int dpm_diag_atomic_replay(dpm_ctx *ctx, const uint32_t *ids, uint64_t n, uint64_t n_vox, double *rate);
+
 /* ---- transport without device allocation -------------------------------
    Not a step of the paper's method (the paper has no counterpart): an entry
    point for callers that cannot allocate device memory once they are running,

@@ -620,6 +620,45 @@ int dpm_diag_philox(dpm_ctx *c, int n, const uint32_t *ctr, const uint32_t *key,
   return DPM_OK;
 }
 
+int dpm_diag_atomic_replay(dpm_ctx *c, const uint32_t *ids, uint64_t n, uint64_t n_vox, double *rate) {
+  if (!c) return DPM_EINVAL;
+  if (!ids || !rate || n == 0 || n > (1ull << 28) || n_vox == 0 || n_vox > (1ull << 32))
+    return fail(c, DPM_EINVAL, "need 1..2^28 ids over 1..2^32 voxels and an output");
+  for (uint64_t i = 0; i < n; ++i)
+    if (ids[i] >= n_vox) return fail(c, DPM_EINVAL, "voxel id out of range");
+  cudaSetDevice(c->device);
+  unsigned long long *slab = nullptr;
+  uint32_t *d_ids = nullptr;
+  int rc;
+  if ((rc = dalloc(c, &slab, size_t(n_vox)))) return rc;
+  if ((rc = dalloc(c, &d_ids, size_t(n)))) {
+    cudaFree(slab);
+    return rc;
+  }
+  cudaEvent_t ev[2];
+  cudaEventCreate(&ev[0]);
+  cudaEventCreate(&ev[1]);
+  cudaError_t e = cudaMemcpyAsync(d_ids, ids, n * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(slab, 0, n_vox * sizeof(unsigned long long), c->stream);
+  const int blocks = c->sm_count * 8;
+  if (e == cudaSuccess) {
+    launch_atomic_replay(slab, d_ids, n, blocks, c->stream);  // warm-up: slab and ids into L2
+    cudaEventRecord(ev[0], c->stream);
+    launch_atomic_replay(slab, d_ids, n, blocks, c->stream);
+    cudaEventRecord(ev[1], c->stream);
+    e = cudaStreamSynchronize(c->stream);
+  }
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  cudaFree(slab);
+  cudaFree(d_ids);
+  if (e != cudaSuccess) return fail(c, DPM_ECUDA, cudaGetErrorString(e));
+  *rate = double(n) / (ms * 1e-3);
+  return DPM_OK;
+}
+
 int dpm_diag_l2_peaks(dpm_ctx *c, uint64_t ws_bytes, double *out) {
   if (!c) return DPM_EINVAL;
   if (!out || ws_bytes < (1u << 20) || ws_bytes > (64u << 20) || (ws_bytes & (ws_bytes - 1)))

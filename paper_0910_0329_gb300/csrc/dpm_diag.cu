@@ -120,6 +120,17 @@ __global__ void k_l2_read(const float4 *b, size_t n, int passes, float *sink) {
   if (acc == 1.2345e-30f) *sink = acc;  // never true for the zeroed buffer; keeps the loads
 }
 
+// Replay of a deposit address stream: each thread walks the id list with a
+// grid stride and adds 1 at every id (64-bit atomic adds, results unused).
+__global__ void k_atomic_replay(unsigned long long *slab, const uint32_t *ids, size_t n) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    atomicAdd(slab + ids[i], 1ull);
+}
+
+void launch_atomic_replay(unsigned long long *slab, const uint32_t *ids, size_t n, int blocks, cudaStream_t st) {
+  k_atomic_replay<<<blocks, 256, 0, st>>>(slab, ids, n);
+}
+
 void launch_l2_atomic(unsigned long long *a, uint32_t mask, int iters, int blocks, cudaStream_t st) {
   k_l2_atomic<<<blocks, 256, 0, st>>>(a, mask, iters);
 }

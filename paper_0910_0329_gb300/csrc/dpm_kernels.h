@@ -23,6 +23,7 @@ void launch_diag_sample(const DevTables &T, int which, double e, double aux, int
                         cudaStream_t st);
 void launch_diag_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, cudaStream_t st);
 void launch_l2_atomic(unsigned long long *a, uint32_t mask, int iters, int blocks, cudaStream_t st);
+void launch_atomic_replay(unsigned long long *slab, const uint32_t *ids, size_t n, int blocks, cudaStream_t st);
 void launch_l2_read(const float4 *b, size_t n, int passes, float *sink, int blocks, cudaStream_t st);
 
 }  // namespace dpm

@@ -93,6 +93,7 @@ _SIGS = {
     "dpm_diag_sample": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, _P, _P]),
     "dpm_diag_philox": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "dpm_diag_l2_peaks": (C.c_int, [_P, C.c_uint64, _P]),
+    "dpm_diag_atomic_replay": (C.c_int, [_P, _P, C.c_uint64, C.c_uint64, _P]),
     "dpm_run_noalloc": (C.c_int, [_P, C.c_int, C.POINTER(dpm_source), C.c_uint64, C.c_uint64, C.c_uint64, _P]),
     # include/dpm_host.h (host-only table inspection)
     "dpm_host_tables_build": (_P, [C.POINTER(dpm_material), C.c_int, C.POINTER(dpm_table_params), C.c_char_p]),
@@ -268,6 +269,14 @@ def dpm_diag_l2_peaks(ctx, ws_bytes=16 << 20):
     out = np.zeros(2, np.float64)
     _check(ctx, lib().dpm_diag_l2_peaks(ctx, int(ws_bytes), _ptr(out)))
     return float(out[0]), float(out[1])
+
+
+def dpm_diag_atomic_replay(ctx, ids, n_vox) -> float:
+    """64-bit atomic adds per second for the voxel id stream `ids`."""
+    a = np.ascontiguousarray(ids, np.uint32)
+    rate = C.c_double(0.0)
+    _check(ctx, lib().dpm_diag_atomic_replay(ctx, _ptr(a), a.size, int(n_vox), C.byref(rate)))
+    return rate.value
 
 
 def run_opts(kernel=KERNEL_QUEUE, n_batches=0, block_size=0, blocks_per_sm=0, queue_log2=0, refill_min=0,
