@@ -268,9 +268,9 @@ extern "C" int dpm_batch_stats(dpm_ctx *c, dpm_run_stats *st) {
     unsigned long long cnt[kCounterSlots];
     BATCH_TRY(c, cudaMemcpy(cnt, c->d_batch_counters, sizeof(cnt), cudaMemcpyDeviceToHost));
     BATCH_TRY(c, cudaMemset(c->d_batch_counters, 0, sizeof(cnt)));
-    st->emitted = double((long long)cnt[C_EMIT]) / kTallyScale;
-    st->escaped = double((long long)cnt[C_ESC]) / kTallyScale;
-    st->missed = double((long long)cnt[C_MISS]) / kTallyScale;
+    st->emitted = double((long long)cnt[C_EMIT]) / kCounterScale;
+    st->escaped = double((long long)cnt[C_ESC]) / kCounterScale;
+    st->missed = double((long long)cnt[C_MISS]) / kCounterScale;
     st->n_e_steps = cnt[C_ESTEP];
     st->n_g_flights = cnt[C_GFLIGHT];
     st->n_g_interactions = cnt[C_GINT];

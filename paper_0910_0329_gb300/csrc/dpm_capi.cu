@@ -474,18 +474,18 @@ static int read_common(dpm_ctx *c, PhantomState *p, const int64_t *s1_host, dpm_
     std::memset(st, 0, sizeof(*st));
     st->n_histories = p->n_total;
     st->n_batches = int32_t(p->b_total);
-    long long dep = 0;
+    double dep = 0;  // the voxel sum can exceed an int64 of 2^-32 MeV quanta
     if (s1_host) {
-      for (size_t v = 0; v < p->V; ++v) dep += s1_host[v];
+      for (size_t v = 0; v < p->V; ++v) dep += double(s1_host[v]);
     } else {
       std::vector<long long> s1(p->V);
       CUDA_TRY(c, cudaMemcpy(s1.data(), p->d_S1, p->V * sizeof(long long), cudaMemcpyDeviceToHost));
-      for (long long x : s1) dep += x;
+      for (long long x : s1) dep += double(x);
     }
-    st->emitted = double((long long)cnt[C_EMIT]) / kTallyScale;
-    st->escaped = double((long long)cnt[C_ESC]) / kTallyScale;
-    st->missed = double((long long)cnt[C_MISS]) / kTallyScale;
-    st->deposited = double(dep) / kTallyScale;
+    st->emitted = double((long long)cnt[C_EMIT]) / kCounterScale;
+    st->escaped = double((long long)cnt[C_ESC]) / kCounterScale;
+    st->missed = double((long long)cnt[C_MISS]) / kCounterScale;
+    st->deposited = dep / kTallyScale;
     st->n_e_steps = cnt[C_ESTEP];
     st->n_g_flights = cnt[C_GFLIGHT];
     st->n_g_interactions = cnt[C_GINT];

@@ -26,6 +26,8 @@ struct HistSink {
     for (int i = 0; i < C_N; ++i) cnt[i] = 0;
   }
   __device__ __forceinline__ static long long fx(float e) { return __float2ll_rn(e * 4294967296.0f); }
+  // energy counters (coarser quantum, see kCounterScale)
+  __device__ __forceinline__ static long long fxc(float e) { return __float2ll_rn(e * kCounterScaleF); }
   __device__ __forceinline__ void flush() {
     if (pend_v >= 0 && pend_q != 0) {
       atomicAdd(slab + pend_v, (unsigned long long)pend_q);
@@ -44,14 +46,14 @@ struct HistSink {
       pend_q = q;
     }
   }
-  __device__ __forceinline__ void escape(float E) { cnt[C_ESC] += fx(E); }
+  __device__ __forceinline__ void escape(float E) { cnt[C_ESC] += fxc(E); }
   __device__ __forceinline__ void push(const Part &q) {
     ++cnt[C_PUSH];
     if (sp < cap) {
       stack[sp++] = q;
     } else {
       err |= ERR_OVERFLOW;
-      cnt[C_ESC] += fx(q.E + (q.type == POSITRON ? 2.f * kMc2f : 0.f));
+      cnt[C_ESC] += fxc(q.E + (q.type == POSITRON ? 2.f * kMc2f : 0.f));
     }
   }
   __device__ __forceinline__ void error(int e) { err |= e; }
@@ -85,9 +87,9 @@ __global__ void __launch_bounds__(128) k_history(const __grid_constant__ RunPara
     s.slab = R.slabs + (hl / batch_size) * V;
     Part p;
     const bool hit = make_primary(p, R, uint32_t(hl));
-    s.cnt[C_EMIT] += HistSink::fx(p.E);
+    s.cnt[C_EMIT] += HistSink::fxc(p.E);
     if (!hit) {
-      s.cnt[C_MISS] += HistSink::fx(p.E);
+      s.cnt[C_MISS] += HistSink::fxc(p.E);
       continue;
     }
     s.sp = 0;

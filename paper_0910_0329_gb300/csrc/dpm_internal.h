@@ -18,6 +18,11 @@ constexpr double kAlpha = 7.2973525693e-3; // fine-structure constant
 constexpr double kNa = 6.02214076e23;      // Avogadro constant, 1/mol
 constexpr double kMeVtoJ = 1.602176634e-13;
 constexpr double kTallyScale = 4294967296.0; // 2^32 fixed-point quanta per MeV
+// The run's energy counters (emitted, escaped, missed) sum every history's
+// energy, so they use a coarser quantum: 2^63 / 2^24 MeV = 5.5e11 MeV, room
+// for 2e10 histories of 20 MeV; rounding adds ~3e-8 MeV per event.
+constexpr double kCounterScale = 16777216.0;  // 2^24 quanta per MeV
+constexpr float kCounterScaleF = 16777216.0f;
 
 // One inverse-CDF sampling table: rows on a uniform ln(E) grid, columns on a
 // uniform grid in the uniform deviate u; entries are a normalised variable in

@@ -161,6 +161,8 @@ struct QSink {
     for (int i = 0; i < C_N; ++i) cnt[i] = 0;
   }
   __device__ __forceinline__ static long long fx(float e) { return __float2ll_rn(e * 4294967296.0f); }
+  // energy counters (coarser quantum, see kCounterScale)
+  __device__ __forceinline__ static long long fxc(float e) { return __float2ll_rn(e * kCounterScaleF); }
   __device__ __forceinline__ void flush() {
     if (pend_v >= 0 && pend_q != 0) {
       atomicAdd(slab + pend_v, (unsigned long long)pend_q);
@@ -179,7 +181,7 @@ struct QSink {
       pend_q = q;
     }
   }
-  __device__ __forceinline__ void escape(float E) { cnt[C_ESC] += fx(E); }
+  __device__ __forceinline__ void escape(float E) { cnt[C_ESC] += fxc(E); }
   __device__ __forceinline__ void error(int e) { err |= e; }
   __device__ __forceinline__ void count_step() { ++cnt[C_ESTEP]; }
   __device__ __forceinline__ void count_flight() { ++cnt[C_GFLIGHT]; }
@@ -225,7 +227,7 @@ struct QSink {
     shard = __shfl_sync(mask, shard, leader);
     if (shard < 0) {
       err |= ERR_OVERFLOW;
-      cnt[C_ESC] += fx(q.E + (q.type == POSITRON ? 2.f * kMc2f : 0.f));
+      cnt[C_ESC] += fxc(q.E + (q.type == POSITRON ? 2.f * kMc2f : 0.f));
       return;
     }
     const unsigned long long p = base + rank;
@@ -396,8 +398,8 @@ __device__ int refill_source(const RunParams &R, const QDev &Q, unsigned empty, 
       } else {
         hit = make_primary(p, R, uint32_t(hl));
       }
-      sk.cnt[C_EMIT] += QSink::fx(p.E);
-      if (!hit) sk.cnt[C_MISS] += QSink::fx(p.E);
+      sk.cnt[C_EMIT] += QSink::fxc(p.E);
+      if (!hit) sk.cnt[C_MISS] += QSink::fxc(p.E);
       alive = hit;
     }
   }

@@ -215,6 +215,40 @@ def c2_electron_blob128(n_histories=10_000_000, seed=3, phantom_seed=3):
     return Workload("e20_blob128", ph, src, n_histories, seed)
 
 
+def paper_slab_phantom(middle):
+    """The phantom of the paper's experiments (Sec. 3): 30.5 x 30.5 x 30 cm of
+    0.5 x 0.5 x 0.2 cm voxels (61 x 61 x 150), water 0-5 cm, then 5 cm of bone
+    (1.85 g/cm^3) or lung (0.3 g/cm^3, density not given in the paper), then
+    20 cm of water."""
+    nx, ny, nz, dz = 61, 61, 150, 0.2
+    zc = (np.arange(nz) + 0.5) * dz
+    mid = (zc >= 5.0) & (zc < 10.0)
+    m_mid, r_mid = (MAT_BONE, 1.85) if middle == "bone" else (MAT_LUNG, 0.3)
+    mat_z = np.where(mid, m_mid, MAT_WATER).astype(np.uint8)
+    rho_z = np.where(mid, r_mid, 1.0).astype(np.float32)
+    mat = np.broadcast_to(mat_z[:, None, None], (nz, ny, nx)).reshape(-1).copy()
+    rho = np.broadcast_to(rho_z[:, None, None], (nz, ny, nx)).reshape(-1).copy()
+    return Phantom(nx, ny, nz, 0.5, 0.5, dz, mat, rho, name=f"paper_w{middle[0]}w_61x61x150")
+
+
+def paper_case(particle, middle, n_histories=None, seed=7):
+    """One case of the paper's Table 1: a 20 MeV electron (10^7 histories) or
+    6 MV photon (10^9) point source at SSD 90 cm with a 10 x 10 cm field at
+    SAD 100 cm, normally incident on the centre of the paper's slab phantom."""
+    ph = paper_slab_phantom(middle)
+    p = dict(DEFAULT_PARAMS)
+    if particle == ELECTRON:
+        src = axial_source(ph, ELECTRON, SPEC_MONO, 20.0, ssd=90.0, sad=100.0, fx=10.0, fy=10.0)
+        n = n_histories or 10_000_000
+        name = f"paper_e20_w{middle[0]}w"
+    else:
+        src = axial_source(ph, PHOTON, SPEC_6MV, 6.0, ssd=90.0, sad=100.0, fx=10.0, fy=10.0)
+        p["e_max"] = 6.5
+        n = n_histories or 1_000_000_000
+        name = f"paper_6mv_w{middle[0]}w"
+    return Workload(name, ph, src, n, seed, p)
+
+
 WORKLOADS = {
     "e20_wlw_61x61x60": c0_electron_wlw,
     "6mv_wbw_61x61x60": c1_photon_wbw,

@@ -99,3 +99,21 @@ def test_timing_events_stay_bounded_without_reads():
         bst = dpm.dpm_batch_stats(d.ctx)
         assert bst["n_transport_launches"] == 1100 and bst["transport_ms"] > 0
         assert bst["n_histories"] == 22000
+
+
+def test_energy_counters_do_not_wrap_on_large_runs():
+    """The run's energy counters sum the energy of every history: 2e8
+    histories of 20 MeV (4e9 MeV, a beam that misses the phantom) would wrap
+    an int64 counter of 2^-32 MeV quanta; the counters use 2^-24 MeV."""
+    import dataclasses
+
+    wl = W.c0_electron_wlw()
+    src = dataclasses.replace(wl.source, iso=(-80.0, -80.0, 0.0))
+    params = dict(wl.params, e_max=21.0)
+    with dpm.Dpm(0, W.MATERIALS, params) as d:
+        pid = d.load_phantom(wl.phantom)
+        d.run(pid, src, 200_000_000, 3)
+        _, _, raw, st = d.read(pid)
+    assert raw.sum() == 0 and st["error_flags"] == 0
+    assert st["emitted"] == pytest.approx(4.0e9, rel=1e-6)
+    assert st["missed"] == st["emitted"]
