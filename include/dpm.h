@@ -143,6 +143,14 @@ int dpm_load_phantom(dpm_ctx *ctx, int nx, int ny, int nz, double dx, double dy,
                      const uint8_t *mat, const float *rho, int *phantom_id);
 int dpm_free_phantom(dpm_ctx *ctx, int phantom_id);
 
+/* Replace the contents (materials and densities, host arrays of nx*ny*nz
+   entries with the phantom's dimensions) of a loaded phantom without
+   reallocating: waits for earlier work on the context's stream, copies the
+   arrays (page-locked host memory makes the copies faster), recomputes the
+   photon majorant and resets the tally as dpm_reset_tally() does.  Same
+   validation as dpm_load_phantom(). */
+int dpm_update_phantom(dpm_ctx *ctx, int phantom_id, const uint8_t *mat, const float *rho);
+
 /* Build the FP32 device tables (per-material attenuation, range, stopping
    power, hard cross sections, transport mean free path; inverse-CDF sampling
    tables) from FP64 closed forms of the model.  The per-material tables have

@@ -267,6 +267,21 @@ int dpm_set_stream(dpm_ctx *c, void *s) {
   return DPM_OK;
 }
 
+// Validate a phantom's host arrays; its largest material index and the
+// largest density of each material (for the photon majorant).
+static int scan_phantom(dpm_ctx *c, const uint8_t *mat, const float *rho, size_t V, int &max_mat,
+                        double (&rho_max)[DPM_MAX_MAT]) {
+  max_mat = 0;
+  for (int m = 0; m < DPM_MAX_MAT; ++m) rho_max[m] = 0.0;
+  for (size_t v = 0; v < V; ++v) {
+    if (mat[v] >= DPM_MAX_MAT) return fail(c, DPM_EINVAL, "material index >= 16");
+    if (!(rho[v] > 0.f) || !std::isfinite(rho[v])) return fail(c, DPM_EINVAL, "density must be positive and finite");
+    max_mat = std::max(max_mat, int(mat[v]));
+    rho_max[mat[v]] = std::max(rho_max[mat[v]], double(rho[v]));
+  }
+  return DPM_OK;
+}
+
 int dpm_load_phantom(dpm_ctx *c, int nx, int ny, int nz, double dx, double dy, double dz, const uint8_t *mat,
                      const float *rho, int *phantom_id) {
   if (!c) return DPM_EINVAL;
@@ -279,13 +294,8 @@ int dpm_load_phantom(dpm_ctx *c, int nx, int ny, int nz, double dx, double dy, d
   p->nx = nx; p->ny = ny; p->nz = nz;
   p->dx = dx; p->dy = dy; p->dz = dz;
   p->V = size_t(nx) * ny * nz;
-  for (size_t v = 0; v < p->V; ++v) {
-    if (mat[v] >= DPM_MAX_MAT) return fail(c, DPM_EINVAL, "material index >= 16");
-    if (!(rho[v] > 0.f) || !std::isfinite(rho[v])) return fail(c, DPM_EINVAL, "density must be positive and finite");
-    p->max_mat = std::max(p->max_mat, int(mat[v]));
-    p->rho_max[mat[v]] = std::max(p->rho_max[mat[v]], double(rho[v]));
-  }
   int rc;
+  if ((rc = scan_phantom(c, mat, rho, p->V, p->max_mat, p->rho_max))) return rc;
   if ((rc = dalloc(c, &p->d_mat, p->V)) || (rc = dalloc(c, &p->d_rho, p->V)) || (rc = dalloc(c, &p->d_S1, p->V)) ||
       (rc = dalloc(c, &p->d_Q, p->V)) || (rc = dalloc(c, &p->d_counters, size_t(kCounterSlots))) ||
       (rc = dalloc(c, &p->d_inv_nb, size_t(1024))) || (rc = dalloc(c, &p->d_mumax, size_t(kMaxTableNodes)))) {
@@ -365,6 +375,27 @@ int dpm_build_tables(dpm_ctx *c, const dpm_material *mats, int n_mat, const dpm_
   for (auto &ph : c->phantoms)
     if (ph && (rc = update_mumax(c, ph.get()))) return rc;
   return DPM_OK;
+}
+
+int dpm_update_phantom(dpm_ctx *c, int id, const uint8_t *mat, const float *rho) {
+  if (!c) return DPM_EINVAL;
+  PhantomState *p = get_phantom(c, id);
+  if (!p) return fail(c, DPM_EINVAL, "bad phantom id");
+  if (!mat || !rho) return fail(c, DPM_EINVAL, "null pointer");
+  int max_mat = 0;
+  double rho_max[DPM_MAX_MAT];
+  int rc;
+  if ((rc = scan_phantom(c, mat, rho, p->V, max_mat, rho_max))) return rc;
+  cudaSetDevice(c->device);
+  // earlier runs on the old contents must finish before the copies land
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  p->max_mat = max_mat;
+  for (int m = 0; m < DPM_MAX_MAT; ++m) p->rho_max[m] = rho_max[m];
+  CUDA_TRY(c, cudaMemcpyAsync(p->d_mat, mat, p->V, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(p->d_rho, rho, p->V * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  if ((rc = dpm_reset_tally(c, id))) return rc;
+  p->mumax_version = -1;  // new densities: the majorant must be rebuilt
+  return update_mumax(c, p);
 }
 
 int dpm_reset_tally(dpm_ctx *c, int id) {

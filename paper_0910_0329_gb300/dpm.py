@@ -79,6 +79,7 @@ _SIGS = {
     "dpm_load_phantom": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, _P, _P,
                                    C.POINTER(C.c_int)]),
     "dpm_free_phantom": (C.c_int, [_P, C.c_int]),
+    "dpm_update_phantom": (C.c_int, [_P, C.c_int, _P, _P]),
     "dpm_build_tables": (C.c_int, [_P, C.POINTER(dpm_material), C.c_int, C.POINTER(dpm_table_params)]),
     "dpm_run": (C.c_int, [_P, C.c_int, C.POINTER(dpm_source), C.c_uint64, C.c_uint64, C.c_uint64,
                           C.POINTER(dpm_run_opts)]),
@@ -166,6 +167,13 @@ def dpm_load_phantom(ctx, ph: W.Phantom) -> int:
 
 def dpm_free_phantom(ctx, pid: int):
     _check(ctx, lib().dpm_free_phantom(ctx, pid))
+
+
+def dpm_update_phantom(ctx, pid: int, ph: W.Phantom):
+    """New materials and densities for a loaded phantom of the same size."""
+    mat = np.ascontiguousarray(ph.mat, np.uint8)
+    rho = np.ascontiguousarray(ph.rho, np.float32)
+    _check(ctx, lib().dpm_update_phantom(ctx, pid, _ptr(mat), _ptr(rho)))
 
 
 def material_struct(md: dict) -> dpm_material:
@@ -317,6 +325,13 @@ class Dpm:
         pid = dpm_load_phantom(self.ctx, ph)
         self.phantoms[pid] = ph
         return pid
+
+    def update_phantom(self, pid, ph: W.Phantom):
+        old = self.phantoms[pid]
+        if (ph.nx, ph.ny, ph.nz) != (old.nx, old.ny, old.nz):
+            raise ValueError("dpm_update_phantom keeps the phantom's dimensions")
+        dpm_update_phantom(self.ctx, pid, ph)
+        self.phantoms[pid] = ph
 
     def run(self, pid, src, n, seed, first=0, **opts):
         dpm_run(self.ctx, pid, src, first, n, seed, run_opts(**opts) if opts else None)

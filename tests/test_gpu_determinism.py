@@ -107,3 +107,25 @@ def test_full_size_launch_equals_history_kernel(config):
     got, st = run_stats(wl, wl.n_histories, dpm.KERNEL_QUEUE)
     assert st["n_phase_switches"] >= 2
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("order", ["denser_to_lighter", "lighter_to_denser"])
+def test_update_phantom_equals_a_fresh_load(order):
+    """New contents for a loaded phantom of the same size (water/bone/water
+    <-> water/lung/water): the photon majorant and the tally are rebuilt, and
+    the run equals one on a freshly loaded phantom bit for bit (a stale
+    majorant would change the Woodcock flights; one too small would be
+    wrong)."""
+    a, b = W.c1_photon_wbw(), W.c0_electron_wlw()
+    first, second = (a.phantom, b.phantom) if order == "denser_to_lighter" else (b.phantom, a.phantom)
+    with dpm.Dpm(0, W.MATERIALS, a.params) as d:
+        pid = d.load_phantom(first)
+        d.run(pid, a.source, 50000, 3)
+        d.update_phantom(pid, second)
+        d.run(pid, a.source, 200000, 3)
+        _, _, got, st = d.read(pid)
+        fresh = d.load_phantom(second)
+        d.run(fresh, a.source, 200000, 3)
+        _, _, ref, _ = d.read(fresh)
+    assert st["n_histories"] == 200000 and st["error_flags"] == 0
+    assert np.array_equal(got, ref)
