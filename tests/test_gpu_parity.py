@@ -20,11 +20,22 @@ pytestmark = pytest.mark.gpu
 KERNELS = [dpm.KERNEL_HISTORY, dpm.KERNEL_QUEUE]
 WORKERS = os.cpu_count() or 1
 
+def oblique_electrons():
+    """20 MeV electrons at gantry 35 degrees (isocentre 10 cm deep) on the
+    water/lung/water slabs: the beam enters the top face obliquely and
+    crosses the slabs at an angle."""
+    wl = W.c0_electron_wlw()
+    X, Y, _ = wl.phantom.extent
+    src = W.Source(W.ELECTRON, W.SPEC_MONO, 20.0, (X / 2, Y / 2, 10.0), 100.0, 5.0, 5.0, 35.0)
+    return W.Workload("e20_oblique35_wlw", wl.phantom, src, 0, 5, wl.params)
+
+
 # name -> (workload factory, oracle histories, GPU histories)
 CASES = {
     "e20_wlw_61x61x60": (W.c0_electron_wlw, 80000, 800000),
     "6mv_wbw_61x61x60": (W.c1_photon_wbw, 6_000_000, 30_000_000),
     "e20_blob128": (W.c2_electron_blob128, 300000, 3_000_000),
+    "e20_oblique35_wlw": (oblique_electrons, 80000, 800000),
 }
 
 _oracle_cache = {}
@@ -195,3 +206,23 @@ def test_phantom_size_limits(gpu_lib):
                 d.load_phantom(ph)
         ok = W.Phantom(2047, 2, 3, 0.1, 0.1, 0.1, np.zeros(2047 * 6, np.uint8), np.ones(2047 * 6, np.float32))
         d.load_phantom(ok)
+
+
+@pytest.mark.parametrize("kernel", KERNELS, ids=["history", "queue"])
+def test_zero_width_pencil(kernel):
+    """A field of zero size: every primary starts on the central axis (the
+    middle of voxel 30 of 61).  The depth-dose along the axis follows the
+    oracle's."""
+    wl0 = W.c0_electron_wlw()
+    X, Y, _ = wl0.phantom.extent
+    src = W.Source(W.ELECTRON, W.SPEC_MONO, 20.0, (X / 2, Y / 2, 0.0), 100.0, 0.0, 0.0)
+    wl = W.Workload("pencil0", wl0.phantom, src, 0, 13, wl0.params)
+    orc = O.run(wl.phantom, W.MATERIALS, wl.params, src, 40000, 17, workers=WORKERS)
+    dose, sigma, raw, st = gpu_run(wl, 400000, kernel)
+    assert st["error_flags"] == 0 and st["missed"] == 0
+    assert np.isfinite(dose).all() and np.isfinite(sigma).all()
+    # the dose of a pencil sits in a few voxels: compare down to 1 % of D_max
+    r = compare(wl.phantom, dose, sigma, raw, 400000, orc, frac_cut=0.01)
+    print(r)
+    assert r["n_vox"] > 100 and r["pass_frac"] >= 0.9, r
+    assert abs(r["e_rel_diff"]) < max(0.2e-2, 3 * r["e_rel_sigma"]), r
