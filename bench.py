@@ -127,6 +127,30 @@ def profiled_traffic(kernel: str, workload: str, key: str = "traffic_bytes_per_h
     return float(tb.group(1)) if kernel_fingerprint() == fp.group(1) else None
 
 
+def time_to_target(d, pid, wl, chunk, kernel, target=0.01, max_chunks=200):
+    """Run `chunk` histories at a time until sigma/D at D_max <= target;
+    returns the wall time, histories and chunks (device-checked each chunk)."""
+    import torch
+
+    from paper_0910_0329_gb300 import dpm
+
+    dpm.dpm_reset_tally(d.ctx, pid)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n = 0
+    rel = float("inf")
+    k = 0
+    for k in range(1, max_chunks + 1):
+        d.run(pid, wl.source, chunk, wl.seed + 7919, first=n, kernel=kernel)
+        n += chunk
+        dose, sig, _ = dpm.dpm_dmax_sigma(d.ctx, [pid])[0]
+        rel = sig / dose if dose > 0 else float("inf")
+        if rel <= target:
+            break
+    return {"wall_s": time.perf_counter() - t0, "histories": n, "chunks": k, "sigma_rel": rel,
+            "target": target, "chunk": chunk}
+
+
 def max_over_ranks(x, world, local):
     """The largest of the ranks' values (the job takes as long as its slowest
     rank); x itself on one rank."""
@@ -373,6 +397,11 @@ def main():
                       "what": "L1->L2 sectors per history (ncu capture of this kernel) vs L1-bypassing loads "
                               "swept over 16 MiB"},
         "peak_kind": "measured (dpm_diag_l2_peaks, this run)"}
+
+    # time to 1 % sigma at D_max, measured: chunks of the step's histories
+    # with a device-side check of sigma/D at D_max after each (the serving
+    # loop's stop rule), from a fresh tally
+    line["time_to_1pct_sigma_at_dmax_measured"] = time_to_target(d, pid, wl, n, kernel)
 
     if not args.no_e2e:
         line["e2e"] = e2e(args, d, wl, n, kernel, local)
