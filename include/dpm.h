@@ -143,6 +143,12 @@ int dpm_load_phantom(dpm_ctx *ctx, int nx, int ny, int nz, double dx, double dy,
                      const uint8_t *mat, const float *rho, int *phantom_id);
 int dpm_free_phantom(dpm_ctx *ctx, int phantom_id);
 
+/* A new phantom with the geometry, materials, densities and photon majorant
+   of phantom src_id and an empty tally, copied on the device (no host
+   arrays, no wait: the copies are queued on the context's stream).  For
+   several tallies of one geometry, e.g. concurrent dose requests. */
+int dpm_clone_phantom(dpm_ctx *ctx, int src_phantom_id, int *phantom_id);
+
 /* Replace the contents (materials and densities, host arrays of nx*ny*nz
    entries with the phantom's dimensions) of a loaded phantom without
    reallocating: waits for earlier work on the context's stream, copies the

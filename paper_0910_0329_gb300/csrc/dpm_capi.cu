@@ -247,6 +247,7 @@ void dpm_destroy(dpm_ctx *c) {
   free_tables(c);
   queue_free(c->queue);
   cudaFree(c->d_jobs);
+  cudaFree(c->d_dmax_out);
   cudaFree(c->d_batch_counters);
   for (cudaEvent_t e : c->batch_ev) cudaEventDestroy(e);
   if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
@@ -377,6 +378,39 @@ int dpm_build_tables(dpm_ctx *c, const dpm_material *mats, int n_mat, const dpm_
   return DPM_OK;
 }
 
+int dpm_clone_phantom(dpm_ctx *c, int src_id, int *phantom_id) {
+  if (!c) return DPM_EINVAL;
+  PhantomState *s = get_phantom(c, src_id);
+  if (!s) return fail(c, DPM_EINVAL, "bad phantom id");
+  if (!phantom_id) return fail(c, DPM_EINVAL, "null pointer");
+  cudaSetDevice(c->device);
+  auto p = std::make_unique<PhantomState>();
+  p->nx = s->nx; p->ny = s->ny; p->nz = s->nz;
+  p->dx = s->dx; p->dy = s->dy; p->dz = s->dz;
+  p->V = s->V;
+  p->max_mat = s->max_mat;
+  for (int m = 0; m < DPM_MAX_MAT; ++m) p->rho_max[m] = s->rho_max[m];
+  int rc;
+  if ((rc = dalloc(c, &p->d_mat, p->V)) || (rc = dalloc(c, &p->d_rho, p->V)) || (rc = dalloc(c, &p->d_S1, p->V)) ||
+      (rc = dalloc(c, &p->d_Q, p->V)) || (rc = dalloc(c, &p->d_counters, size_t(kCounterSlots))) ||
+      (rc = dalloc(c, &p->d_inv_nb, size_t(1024))) || (rc = dalloc(c, &p->d_mumax, size_t(kMaxTableNodes)))) {
+    free_phantom(p.get());
+    return rc;
+  }
+  // device-to-device, ordered on the context's stream after any pending work
+  CUDA_TRY(c, cudaMemcpyAsync(p->d_mat, s->d_mat, p->V, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(p->d_rho, s->d_rho, p->V * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(p->d_mumax, s->d_mumax, kMaxTableNodes * sizeof(float), cudaMemcpyDeviceToDevice,
+                              c->stream));
+  p->mumax_version = s->mumax_version;
+  CUDA_TRY(c, cudaMemsetAsync(p->d_S1, 0, p->V * sizeof(long long), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(p->d_Q, 0, p->V * sizeof(double), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(p->d_counters, 0, kCounterSlots * sizeof(unsigned long long), c->stream));
+  c->phantoms.push_back(std::move(p));
+  *phantom_id = int(c->phantoms.size()) - 1;
+  return DPM_OK;
+}
+
 int dpm_update_phantom(dpm_ctx *c, int id, const uint8_t *mat, const float *rho) {
   if (!c) return DPM_EINVAL;
   PhantomState *p = get_phantom(c, id);
@@ -469,16 +503,24 @@ int dpm_dmax_sigma(dpm_ctx *c, const int *ids, int n, double *out) {
       if (rc) return rc;
     }
   }
+  if (n > c->dmax_cap) {
+    cudaFree(c->d_dmax_out);
+    c->d_dmax_out = nullptr;
+    c->dmax_cap = 0;
+    int rc = dalloc(c, &c->d_dmax_out, size_t(3) * size_t(n));
+    if (rc) return rc;
+    c->dmax_cap = n;
+  }
+  // every request's result lands in one device array: one copy back
   for (int i = 0; i < n; ++i) {
     PhantomState *p = ps[i];
     launch_dmax(p->d_S1, p->d_Q, p->d_rho, p->V, double(p->n_total), double(p->b_total), p->dx * p->dy * p->dz,
-                p->d_dmax, reinterpret_cast<double *>(p->d_dmax + 1), c->sm_count, c->stream);
+                p->d_dmax, c->d_dmax_out + 3 * i, c->sm_count, c->stream);
   }
   CUDA_TRY(c, cudaGetLastError());
   const int src = dpm_sync(c);
   if (src == DPM_ECUDA) return src;
-  for (int i = 0; i < n; ++i)
-    CUDA_TRY(c, cudaMemcpy(out + 3 * i, ps[i]->d_dmax + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost));
+  if (n > 0) CUDA_TRY(c, cudaMemcpy(out, c->d_dmax_out, 3 * sizeof(double) * size_t(n), cudaMemcpyDeviceToHost));
   return src;
 }
 

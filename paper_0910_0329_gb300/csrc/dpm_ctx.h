@@ -66,6 +66,8 @@ struct dpm_ctx {
   dpm::QueueState queue;
   // batches
   dpm::DevJob *d_jobs = nullptr;               // job table, kMaxJobs entries
+  double *d_dmax_out = nullptr;                // dpm_dmax_sigma results, 3 per phantom [dmax_cap]
+  int dmax_cap = 0;
   unsigned long long *d_batch_counters = nullptr;  // [kCounterSlots]
   std::vector<cudaEvent_t> batch_ev;           // start/end pairs since the last dpm_batch_stats
   double batch_folded_ms = 0;                  // times of pairs retired early (see kMaxPendingEvents)

@@ -80,6 +80,7 @@ _SIGS = {
                                    C.POINTER(C.c_int)]),
     "dpm_free_phantom": (C.c_int, [_P, C.c_int]),
     "dpm_update_phantom": (C.c_int, [_P, C.c_int, _P, _P]),
+    "dpm_clone_phantom": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
     "dpm_build_tables": (C.c_int, [_P, C.POINTER(dpm_material), C.c_int, C.POINTER(dpm_table_params)]),
     "dpm_run": (C.c_int, [_P, C.c_int, C.POINTER(dpm_source), C.c_uint64, C.c_uint64, C.c_uint64,
                           C.POINTER(dpm_run_opts)]),
@@ -167,6 +168,13 @@ def dpm_load_phantom(ctx, ph: W.Phantom) -> int:
 
 def dpm_free_phantom(ctx, pid: int):
     _check(ctx, lib().dpm_free_phantom(ctx, pid))
+
+
+def dpm_clone_phantom(ctx, pid: int) -> int:
+    """A device copy of phantom `pid` (same contents and majorant, empty tally)."""
+    out = C.c_int(-1)
+    _check(ctx, lib().dpm_clone_phantom(ctx, pid, C.byref(out)))
+    return out.value
 
 
 def dpm_update_phantom(ctx, pid: int, ph: W.Phantom):
@@ -325,6 +333,11 @@ class Dpm:
         pid = dpm_load_phantom(self.ctx, ph)
         self.phantoms[pid] = ph
         return pid
+
+    def clone_phantom(self, pid) -> int:
+        new = dpm_clone_phantom(self.ctx, pid)
+        self.phantoms[new] = self.phantoms[pid]
+        return new
 
     def update_phantom(self, pid, ph: W.Phantom):
         old = self.phantoms[pid]

@@ -119,7 +119,10 @@ class Server:
             return self.free[g].pop()
         if self.used + self.slot_bytes[g] > self.budget:
             return None
-        pid = self.d.load_phantom(self.geoms[g])
+        # a further slot of a geometry already on the device is a device copy
+        # (no host scan, upload or wait); the first one is loaded from the host
+        same = [pid for pid, gg in self.slot_geom.items() if gg == g]
+        pid = self.d.clone_phantom(same[0]) if same else self.d.load_phantom(self.geoms[g])
         self.slot_pid[pid] = pid
         self.slot_geom[pid] = g
         self.used += self.slot_bytes[g]

@@ -129,3 +129,23 @@ def test_update_phantom_equals_a_fresh_load(order):
         _, _, ref, _ = d.read(fresh)
     assert st["n_histories"] == 200000 and st["error_flags"] == 0
     assert np.array_equal(got, ref)
+
+
+def test_clone_phantom_equals_a_fresh_load():
+    """A device copy of a phantom (contents and majorant, empty tally) runs
+    bit for bit like a freshly loaded one, also while the source phantom
+    keeps its own tally."""
+    wl = W.c1_photon_wbw()
+    with dpm.Dpm(0, W.MATERIALS, wl.params) as d:
+        src = d.load_phantom(wl.phantom)
+        d.run(src, wl.source, 100000, 9)
+        twin = d.clone_phantom(src)
+        d.run(twin, wl.source, 200000, 3)
+        _, _, got, st = d.read(twin)
+        _, _, src_raw, src_st = d.read(src)
+        fresh = d.load_phantom(wl.phantom)
+        d.run(fresh, wl.source, 200000, 3)
+        _, _, ref, _ = d.read(fresh)
+    assert st["n_histories"] == 200000 and src_st["n_histories"] == 100000
+    assert np.array_equal(got, ref)
+    assert not np.array_equal(src_raw, ref)
