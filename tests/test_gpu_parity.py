@@ -30,12 +30,33 @@ def oblique_electrons():
     return W.Workload("e20_oblique35_wlw", wl.phantom, src, 0, 5, wl.params)
 
 
+def electrons_bone():
+    """The paper's other electron case: 20 MeV electrons (SSD 100, 5x5 cm)
+    through a bone slab, water 0-3 cm / bone (1.85) 3-7 cm / water."""
+    wl = W.c0_electron_wlw()
+    ph = W.slab_phantom(61, 61, 60, 0.5, [(0, 3, W.MAT_WATER, 1.0), (3, 7, W.MAT_BONE, 1.85),
+                                          (7, 1e9, W.MAT_WATER, 1.0)], name="wbw_61x61x60")
+    return W.Workload("e20_wbw_61x61x60", ph, wl.source, 0, 6, wl.params)
+
+
+def photons_lung():
+    """The paper's other photon case: 6 MV (SSD 90, 10x10 cm at SAD 100)
+    through a lung slab, water 0-3 cm / lung (0.3) 3-10 cm / water."""
+    wl = W.c1_photon_wbw()
+    ph = W.slab_phantom(61, 61, 60, 0.5, [(0, 3, W.MAT_WATER, 1.0), (3, 10, W.MAT_LUNG, 0.3),
+                                          (10, 1e9, W.MAT_WATER, 1.0)], name="wlw_61x61x60")
+    src = W.axial_source(ph, W.PHOTON, W.SPEC_6MV, 6.0, ssd=90.0, sad=100.0, fx=10.0, fy=10.0)
+    return W.Workload("6mv_wlw_61x61x60", ph, src, 0, 8, wl.params)
+
+
 # name -> (workload factory, oracle histories, GPU histories)
 CASES = {
     "e20_wlw_61x61x60": (W.c0_electron_wlw, 80000, 800000),
     "6mv_wbw_61x61x60": (W.c1_photon_wbw, 6_000_000, 30_000_000),
     "e20_blob128": (W.c2_electron_blob128, 300000, 3_000_000),
     "e20_oblique35_wlw": (oblique_electrons, 80000, 800000),
+    "e20_wbw_61x61x60": (electrons_bone, 80000, 800000),
+    "6mv_wlw_61x61x60": (photons_lung, 6_000_000, 30_000_000),
 }
 
 _oracle_cache = {}
