@@ -219,6 +219,99 @@ int dpm_dmax_sigma(dpm_ctx *ctx, const int *phantom_ids, int n, double *out);
 /* Wait for queued work; reports device-side errors of earlier runs. */
 int dpm_sync(dpm_ctx *ctx);
 
+/* ---- serving: dose requests with continuous batching --------------------
+   Not a step of the paper's method (it runs one problem per program,
+   Sec. 2.2).  A server works on one context.  A request is a beam on a
+   geometry: a phantom loaded in the context.  An admitted request gets a
+   tally slot, a device copy of its geometry (dpm_clone_phantom), while the
+   slots' device memory stays within hbm_budget_bytes.  Each call of
+   dpm_server_round():
+   - admits pending requests in submission order;
+   - takes the active requests oldest first while their next chunks fit
+     round_budget histories (the oldest always);
+   - transports them in one dpm_run_batch();
+   - measures each one's D_max and sigma on the device (dpm_dmax_sigma);
+   - marks done the requests whose relative sigma at D_max reached
+     target_rel_sigma.
+   A request's first round has first_chunk histories.  With `adaptive`, later
+   rounds run about n (r/target)^2 * overshoot - n histories (r the relative
+   sigma after n histories), within [first_chunk, max_chunk].  Round sizes,
+   history ranges (consecutive, with the request's seed) and the stop
+   decision depend only on the request's own tally, so its result is the
+   same alone or with any other requests.  A done request keeps its slot,
+   whose tally dpm_read_dose(ctx, status.slot, ...) reads, until
+   dpm_server_release() returns the slot to its geometry's pool.  A slot
+   that does not fit the budget frees released slots of other geometries
+   first (dpm_free_phantom).  The server keeps its slots as phantoms of the
+   context; they are freed with the context, not with the server.  Errors of
+   a round (queue overflow, timed-out wait, device allocation) are returned
+   by dpm_server_round(), with the message in dpm_last_error(ctx); the
+   server's calls are not thread-safe (one caller per context). */
+typedef struct dpm_server dpm_server;
+typedef struct {
+    double target_rel_sigma;   /* stop at sigma/D at D_max <= this, in (0, 1) */
+    uint64_t first_chunk;      /* histories of a request's first round (0 = 200000) */
+    uint64_t max_chunk;        /* cap of a later round (0 = 32 * first_chunk; <= 2^31-1) */
+    double overshoot;          /* factor on the histories a later round aims at (0 = 1.15) */
+    uint64_t round_budget;     /* histories per round (0 = 40 * first_chunk) */
+    int n_batches;             /* history batches per round for sigma (0 = 10) */
+    int max_active;            /* admitted requests at most (0 or > 1024 = 1024) */
+    int adaptive;              /* 1: size later rounds from sigma; 0: every round first_chunk */
+    uint64_t hbm_budget_bytes; /* device memory of all slots (0 = no limit) */
+} dpm_serve_opts;
+enum { DPM_REQ_PENDING = 0, DPM_REQ_ACTIVE = 1, DPM_REQ_DONE = 2, DPM_REQ_RELEASED = 3 };
+typedef struct {
+    int state;                 /* DPM_REQ_* */
+    int slot;                  /* phantom id of the request's tally slot (-1 before admission / after release) */
+    uint64_t histories;        /* transported so far */
+    int rounds;
+    double rel_sigma;          /* relative sigma at D_max after the last round (inf before) */
+    double dose_max;           /* D_max, Gy per history */
+    int dmax_voxel;
+} dpm_request_status;
+/* A server on ctx (opts may be NULL: all defaults; target_rel_sigma must then
+   be set, so NULL gives DPM_EINVAL).  DPM_EINVAL for invalid options. */
+int dpm_server_create(dpm_ctx *ctx, const dpm_serve_opts *opts, dpm_server **server);
+/* Frees the server's host state; its slots stay phantoms of the context. */
+void dpm_server_destroy(dpm_server *server);
+/* Queue a request on geometry_id (a loaded phantom, not a slot); *request_id
+   numbers requests from 0 in submission order.  The source is copied.
+   DPM_EINVAL for a bad geometry id or a null pointer. */
+int dpm_server_submit(dpm_server *server, int geometry_id, const dpm_source *src, uint64_t seed, int *request_id);
+/* One round (synchronous); *n_completed receives the requests it finished.
+   Does nothing when no request is active or admissible. */
+int dpm_server_round(dpm_server *server, int *n_completed);
+/* A request's state and statistics; DPM_EINVAL for a bad id. */
+int dpm_server_status(dpm_server *server, int request_id, dpm_request_status *status);
+typedef struct {
+    int n_pending;             /* submitted, not yet admitted */
+    int n_active;              /* admitted, not done */
+    int n_done;                /* done, not yet released */
+    int max_active;            /* most requests active in one round */
+    uint64_t n_rounds;         /* rounds that ran a batch */
+    uint64_t n_completed;      /* requests that reached the target */
+    uint64_t histories;        /* histories transported by all rounds */
+    uint64_t slot_bytes;       /* device bytes the slots hold now (counted as dpm_server_slot_bytes) */
+    uint64_t peak_slot_bytes;  /* most slot bytes held at once */
+    double gpu_ms;             /* device time of the rounds' batches (CUDA events) */
+} dpm_server_info;
+/* The server's counters; DPM_EINVAL for a null pointer. */
+int dpm_server_info_get(dpm_server *server, dpm_server_info *info);
+/* Device bytes one slot of geometry_id counts against hbm_budget_bytes:
+   material, density, S1, Q, n_batches batch slabs per voxel and the fixed
+   per-phantom buffers.  DPM_EINVAL for a bad geometry id. */
+int dpm_server_slot_bytes(dpm_server *server, int geometry_id, uint64_t *bytes);
+/* Return a done request's slot (tally reset) to its geometry's pool;
+   DPM_ESTATE unless the request is done. */
+int dpm_server_release(dpm_server *server, int request_id);
+/* The server's policies as pure host functions (no context, no GPU):
+   the histories of a request's next round after `histories` at relative
+   sigma `rel_sigma` (0 for invalid options), and the round selection over
+   requests oldest first (next_n[i] histories each; fills chosen with the
+   indexes taken; returns their count, -1 for bad arguments). */
+uint64_t dpm_serve_next_chunk(const dpm_serve_opts *opts, uint64_t histories, double rel_sigma);
+int dpm_serve_select(const uint64_t *next_n, int n, uint64_t budget, int *chosen);
+
 /* ---- diagnostics used by the parity tests ------------------------------ */
 
 /* Evaluate the device tables at n energies (host arrays).  which: 0 mu/rho

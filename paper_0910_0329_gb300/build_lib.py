@@ -15,7 +15,7 @@ INC = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libdpm.so")
 
-CU = ["dpm_capi.cu", "dpm_history.cu", "dpm_queue.cu", "dpm_diag.cu", "dpm_noalloc.cu", "dpm_batch.cu"]
+CU = ["dpm_capi.cu", "dpm_history.cu", "dpm_queue.cu", "dpm_diag.cu", "dpm_noalloc.cu", "dpm_batch.cu", "dpm_serve.cu"]
 CPP = ["dpm_tables.cpp", "dpm_host_tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no implicit FMA contraction, so every kernel computes a particle

@@ -198,7 +198,7 @@ extern "C" int dpm_run_batch(dpm_ctx *c, const dpm_job *jobs, int n_jobs, const 
                                  uint64_t(o.physics_flags), uint64_t(o.timeout_s * 1e6), uint64_t(b.tab.size()),
                                  uint64_t(b.total)};
     for (size_t j = 0; j < b.tab.size(); ++j) {
-      sig.push_back(uint64_t(reinterpret_cast<uintptr_t>(b.ph[j])));
+      sig.push_back(b.ph[j]->uid);
       sig.push_back(uint64_t(reinterpret_cast<uintptr_t>(b.ph[j]->d_slabs)));
       sig.push_back(b.tab[j].n);
       sig.push_back(uint64_t(b.nb[j]));
@@ -207,7 +207,7 @@ extern "C" int dpm_run_batch(dpm_ctx *c, const dpm_job *jobs, int n_jobs, const 
     // range, seed and beam become part of the shape
     for (size_t j = 0; j < b.solo.size(); ++j) {
       const RunParams &Rs = b.solo[j];
-      sig.push_back(uint64_t(reinterpret_cast<uintptr_t>(b.solo_ph[j])));
+      sig.push_back(b.solo_ph[j]->uid);
       sig.push_back(uint64_t(reinterpret_cast<uintptr_t>(Rs.slabs)));
       sig.push_back(Rs.first);
       sig.push_back(Rs.n);
@@ -216,6 +216,8 @@ extern "C" int dpm_run_batch(dpm_ctx *c, const dpm_job *jobs, int n_jobs, const 
       const uint32_t *sw = reinterpret_cast<const uint32_t *>(&Rs.S);
       for (size_t w = 0; w < sizeof(Rs.S) / 4; ++w) sig.push_back(sw[w]);
     }
+    // phantoms enter by uid: a freed phantom's host or device addresses may
+    // come back in a new one, whose pointers a stale graph would not hold
     if (!c->batch_exec || sig != c->batch_sig) {
       if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
       c->batch_exec = nullptr;

@@ -313,6 +313,7 @@ int dpm_load_phantom(dpm_ctx *c, int nx, int ny, int nz, double dx, double dy, d
     free_phantom(p.get());
     return rc;
   }
+  p->uid = c->next_phantom_uid++;
   c->phantoms.push_back(std::move(p));
   *phantom_id = int(c->phantoms.size()) - 1;
   return DPM_OK;
@@ -406,6 +407,7 @@ int dpm_clone_phantom(dpm_ctx *c, int src_id, int *phantom_id) {
   CUDA_TRY(c, cudaMemsetAsync(p->d_S1, 0, p->V * sizeof(long long), c->stream));
   CUDA_TRY(c, cudaMemsetAsync(p->d_Q, 0, p->V * sizeof(double), c->stream));
   CUDA_TRY(c, cudaMemsetAsync(p->d_counters, 0, kCounterSlots * sizeof(unsigned long long), c->stream));
+  p->uid = c->next_phantom_uid++;
   c->phantoms.push_back(std::move(p));
   *phantom_id = int(c->phantoms.size()) - 1;
   return DPM_OK;

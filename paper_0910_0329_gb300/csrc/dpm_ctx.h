@@ -22,6 +22,7 @@ constexpr int kMaxTableNodes = 65536;  // upper bound of dpm_table_params.n_e
 constexpr size_t kMaxPendingEvents = 3 * 1024;
 
 struct PhantomState {
+  uint64_t uid = 0;  // unique within the context, never reused (keys the batch graph)
   int nx = 0, ny = 0, nz = 0;
   double dx = 0, dy = 0, dz = 0;
   size_t V = 0;
@@ -62,6 +63,7 @@ struct dpm_ctx {
   dpm::DevTables dt{};
   std::vector<void *> table_mem;
   std::vector<std::unique_ptr<dpm::PhantomState>> phantoms;
+  uint64_t next_phantom_uid = 1;
   int *d_err = nullptr;
   dpm::QueueState queue;
   // batches

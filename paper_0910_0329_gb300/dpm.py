@@ -57,6 +57,26 @@ class dpm_job(C.Structure):
                 ("n_histories", C.c_uint64), ("seed", C.c_uint64)]
 
 
+class dpm_serve_opts(C.Structure):
+    _fields_ = [("target_rel_sigma", C.c_double), ("first_chunk", C.c_uint64), ("max_chunk", C.c_uint64),
+                ("overshoot", C.c_double), ("round_budget", C.c_uint64), ("n_batches", C.c_int),
+                ("max_active", C.c_int), ("adaptive", C.c_int), ("hbm_budget_bytes", C.c_uint64)]
+
+
+class dpm_request_status(C.Structure):
+    _fields_ = [("state", C.c_int), ("slot", C.c_int), ("histories", C.c_uint64), ("rounds", C.c_int),
+                ("rel_sigma", C.c_double), ("dose_max", C.c_double), ("dmax_voxel", C.c_int)]
+
+
+class dpm_server_info(C.Structure):
+    _fields_ = [("n_pending", C.c_int), ("n_active", C.c_int), ("n_done", C.c_int), ("max_active", C.c_int),
+                ("n_rounds", C.c_uint64), ("n_completed", C.c_uint64), ("histories", C.c_uint64),
+                ("slot_bytes", C.c_uint64), ("peak_slot_bytes", C.c_uint64), ("gpu_ms", C.c_double)]
+
+
+REQ_PENDING, REQ_ACTIVE, REQ_DONE, REQ_RELEASED = 0, 1, 2, 3
+
+
 class dpm_run_stats(C.Structure):
     _fields_ = [("n_histories", C.c_uint64), ("n_batches", C.c_int32), ("error_flags", C.c_int32),
                 ("emitted", C.c_double), ("deposited", C.c_double), ("escaped", C.c_double), ("missed", C.c_double),
@@ -97,6 +117,16 @@ _SIGS = {
     "dpm_diag_l2_peaks": (C.c_int, [_P, C.c_uint64, _P]),
     "dpm_diag_atomic_replay": (C.c_int, [_P, _P, C.c_uint64, C.c_uint64, _P]),
     "dpm_run_noalloc": (C.c_int, [_P, C.c_int, C.POINTER(dpm_source), C.c_uint64, C.c_uint64, C.c_uint64, _P]),
+    "dpm_server_create": (C.c_int, [_P, C.POINTER(dpm_serve_opts), C.POINTER(_P)]),
+    "dpm_server_destroy": (None, [_P]),
+    "dpm_server_submit": (C.c_int, [_P, C.c_int, C.POINTER(dpm_source), C.c_uint64, C.POINTER(C.c_int)]),
+    "dpm_server_round": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "dpm_server_status": (C.c_int, [_P, C.c_int, C.POINTER(dpm_request_status)]),
+    "dpm_server_info_get": (C.c_int, [_P, C.POINTER(dpm_server_info)]),
+    "dpm_server_slot_bytes": (C.c_int, [_P, C.c_int, C.POINTER(C.c_uint64)]),
+    "dpm_server_release": (C.c_int, [_P, C.c_int]),
+    "dpm_serve_next_chunk": (C.c_uint64, [C.POINTER(dpm_serve_opts), C.c_uint64, C.c_double]),
+    "dpm_serve_select": (C.c_int, [_P, C.c_int, C.c_uint64, _P]),
     # include/dpm_host.h (host-only table inspection)
     "dpm_host_tables_build": (_P, [C.POINTER(dpm_material), C.c_int, C.POINTER(dpm_table_params), C.c_char_p]),
     "dpm_host_tables_free": (None, [_P]),
@@ -293,6 +323,71 @@ def dpm_diag_atomic_replay(ctx, ids, n_vox) -> float:
     rate = C.c_double(0.0)
     _check(ctx, lib().dpm_diag_atomic_replay(ctx, _ptr(a), a.size, int(n_vox), C.byref(rate)))
     return rate.value
+
+
+def serve_opts(target=0.01, first_chunk=0, max_chunk=0, overshoot=0.0, round_budget=0, n_batches=0, max_active=0,
+               adaptive=1, hbm_budget_bytes=0) -> dpm_serve_opts:
+    return dpm_serve_opts(target, first_chunk, max_chunk, overshoot, round_budget, n_batches, max_active, adaptive,
+                          hbm_budget_bytes)
+
+
+class Server:
+    """The library's request server (dpm_server_*) on a context."""
+
+    def __init__(self, ctx, opts: dpm_serve_opts):
+        self.ctx = ctx
+        h = _P()
+        _check(ctx, lib().dpm_server_create(ctx, C.byref(opts), C.byref(h)))
+        self.h = h
+
+    def _chk(self, rc):
+        _check(self.ctx, rc)
+
+    def submit(self, geometry_id, src, seed) -> int:
+        rid = C.c_int(-1)
+        self._chk(lib().dpm_server_submit(self.h, geometry_id, C.byref(source_struct(src)), seed, C.byref(rid)))
+        return rid.value
+
+    def round(self) -> int:
+        done = C.c_int(0)
+        self._chk(lib().dpm_server_round(self.h, C.byref(done)))
+        return done.value
+
+    def status(self, rid) -> dict:
+        st = dpm_request_status()
+        self._chk(lib().dpm_server_status(self.h, rid, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def info(self) -> dict:
+        st = dpm_server_info()
+        self._chk(lib().dpm_server_info_get(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def slot_bytes(self, geometry_id) -> int:
+        b = C.c_uint64()
+        self._chk(lib().dpm_server_slot_bytes(self.h, geometry_id, C.byref(b)))
+        return b.value
+
+    def release(self, rid):
+        self._chk(lib().dpm_server_release(self.h, rid))
+
+    def close(self):
+        if self.h:
+            lib().dpm_server_destroy(self.h)
+            self.h = None
+
+
+def serve_next_chunk(opts: dpm_serve_opts, histories, rel_sigma) -> int:
+    return int(lib().dpm_serve_next_chunk(C.byref(opts), int(histories), float(rel_sigma)))
+
+
+def serve_select(next_n, budget) -> list:
+    a = np.ascontiguousarray(next_n, np.uint64)
+    out = np.zeros(max(a.size, 1), np.int32)
+    k = lib().dpm_serve_select(_ptr(a), a.size, int(budget), _ptr(out))
+    if k < 0:
+        raise ValueError("bad arguments")
+    return out[:k].tolist()
 
 
 def run_opts(kernel=KERNEL_QUEUE, n_batches=0, block_size=0, blocks_per_sm=0, queue_log2=0, refill_min=0,

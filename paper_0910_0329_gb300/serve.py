@@ -1,30 +1,23 @@
-"""Dose-request server with continuous batching on one GPU.
+"""Dose requests that arrive over time, served with continuous batching on one
+GPU by the library's server (dpm_server_* in include/dpm.h).
 
-Requests (a beam on one of the resident phantom geometries) arrive over time.
-Each admitted request owns a tally slot (a device copy of its geometry with
-its own integer tally); admission is limited by an HBM budget that counts the
-tables, the queue memory and every slot.  The server works in rounds: every
-round transports the next chunk of histories of all active requests in one
-batched persistent launch (dpm_run_batch), then asks the device for each
-request's D_max and its sigma (dpm_dmax_sigma) and retires the requests that
-reached the target relative uncertainty.  Requests that arrive meanwhile join
-at the next round, so work from different requests overlaps on the device.
+The policies are the library's: each admitted request owns a tally slot (a
+device copy of its geometry with its own integer tally) while the slots fit
+an HBM budget; every round transports the next chunks of the oldest active
+requests that fit the round's history budget in one batched persistent launch
+(dpm_run_batch), finds each one's D_max and its sigma on the device
+(dpm_dmax_sigma) and retires those that reached the target relative sigma.  A
+request's first round transports `chunk` histories; with `adaptive`, a later
+round is sized from the request's own relative sigma r after n histories
+(about n*(r/target)^2 are needed in all).  Round sizes, history ranges and the
+stop decision depend only on the request's own tally, so its result is the
+same alone or in any mix.
 
-A request's first round transports `chunk` histories.  With `adaptive`, each
-later round is sized from the request's own relative sigma at D_max: with r
-after n histories, about n*(r/target)^2 are needed in all, so the next round
-transports that (times `overshoot`, within [chunk, max_chunk]) minus n; most
-requests then finish in two rounds instead of n_final/chunk.  Without it every
-round transports `chunk`.  Round sizes, history ranges (consecutive, with the
-request's own seed) and the stop decision depend only on the request's own
-tally: its result is the same alone or in any mix.
-
-A round takes the active requests oldest first until their next chunks reach
-`round_budget` histories (at least one request).  Under load this keeps the
-server close to first-come-first-served -- which minimises the mean latency
-of similar requests -- while younger requests fill the round's tail, instead
-of advancing every active request together (processor sharing, whose rounds
-and latencies grow with the queue).
+This module adds what a caller around the library does: it loads each
+geometry once (the template its slots copy), submits requests when their
+arrival time comes, calls a round while there is work, records arrival,
+admission and completion times, reads a finished request's tally if asked and
+releases its slot.
 """
 from __future__ import annotations
 
@@ -49,7 +42,6 @@ class Request:
     done: float | None = None
     histories: int = 0
     rounds: int = 0
-    next_n: int = 0
     rel_sigma: float = math.inf
     dose_max: float = 0.0
     raw: np.ndarray | None = None
@@ -89,144 +81,100 @@ class Server:
                  max_active=1024, keep_results=False, seed_base=10 ** 6, device=0, stream=None, adaptive=True,
                  max_chunk=None, overshoot=1.15, round_budget=None):
         self.d = dpm.Dpm(device, W.MATERIALS, params or W.DEFAULT_PARAMS, stream=stream)
-        self.geoms = list(geometries)
-        self.chunk = int(chunk)
-        self.adaptive = bool(adaptive)
-        self.max_chunk = int(max_chunk) if max_chunk else 32 * self.chunk
-        self.overshoot = float(overshoot)
-        self.round_budget = int(round_budget) if round_budget else 40 * self.chunk
-        self.target = float(target)
-        self.n_batches = int(n_batches)
-        self.max_active = int(max_active)
-        self.keep = keep_results
-        self.seed_base = seed_base
-        self.budget = int(hbm_budget)
-        # fixed device memory: tables (~1 MB) and the queue (upper bound of the default layout)
-        self.fixed = 64 << 20
-        self.fixed += 2 * 1216 * (1 << 14) * 13 * 4
-        self.slot_bytes = [g.n_vox * (1 + 4 + 8 + 8 + 8 * self.n_batches) + (512 << 10) for g in self.geoms]
-        self.free = {i: [] for i in range(len(self.geoms))}
-        self.slot_pid = {}   # slot id -> phantom id
-        self.slot_geom = {}
-        self.used = self.fixed
-        self.pending: list[Request] = []
-        self.active: list[Request] = []
+        self.srv = None
+        try:
+            self.geoms = list(geometries)
+            self.keep = keep_results
+            self.seed_base = seed_base
+            self.budget = int(hbm_budget)
+            # each geometry is resident once: the template its slots copy
+            self.template = [self.d.load_phantom(g) for g in self.geoms]
+            opts = dict(target=target, first_chunk=int(chunk), max_chunk=int(max_chunk or 0), overshoot=overshoot,
+                        round_budget=int(round_budget or 0), n_batches=n_batches, max_active=max_active,
+                        adaptive=int(bool(adaptive)))
+            probe = dpm.Server(self.d.ctx, dpm.serve_opts(**opts))
+            try:
+                self.slot_bytes = [probe.slot_bytes(t) for t in self.template]
+            finally:
+                probe.close()
+            # fixed device memory: tables (~1 MB), the queue (an upper bound of
+            # its default layout) and the templates; the rest is for slots
+            self.fixed = (64 << 20) + 2 * 1216 * (1 << 14) * 13 * 4 + sum(self.slot_bytes)
+            if self.budget <= self.fixed:
+                raise ValueError(f"hbm_budget {self.budget} is below the fixed {self.fixed} bytes")
+            self.srv = dpm.Server(self.d.ctx, dpm.serve_opts(**opts, hbm_budget_bytes=self.budget - self.fixed))
+        except BaseException:
+            self.d.close()
+            raise
         self.stats = ServeStats()
 
-    # -- slots ------------------------------------------------------------
-    def _take_slot(self, g):
-        if self.free[g]:
-            return self.free[g].pop()
-        if self.used + self.slot_bytes[g] > self.budget:
-            return None
-        # a further slot of a geometry already on the device is a device copy
-        # (no host scan, upload or wait); the first one is loaded from the host
-        same = [pid for pid, gg in self.slot_geom.items() if gg == g]
-        pid = self.d.clone_phantom(same[0]) if same else self.d.load_phantom(self.geoms[g])
-        self.slot_pid[pid] = pid
-        self.slot_geom[pid] = g
-        self.used += self.slot_bytes[g]
-        self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)
-        return pid
+    @property
+    def used(self):
+        """Device bytes counted against the budget now: fixed part and slots."""
+        return self.fixed + self.srv.info()["slot_bytes"]
 
-    def _release(self, slot):
-        dpm.dpm_reset_tally(self.d.ctx, slot)
-        self.free[self.slot_geom[slot]].append(slot)
-
-    # -- requests ---------------------------------------------------------
-    def submit(self, req: Request):
-        self.pending.append(req)
-
-    def _admit(self, now):
-        still = []
-        for r in self.pending:
-            if len(self.active) >= self.max_active:
-                still.append(r)
+    def _collect(self, waiting, admitted_by, now):
+        """Statuses after a round: admission times, progress, and the done
+        requests' results (their slots are released)."""
+        for rid in list(waiting):
+            r = waiting[rid]
+            st = self.srv.status(rid)
+            if st["state"] == dpm.REQ_PENDING:
                 continue
-            slot = self._take_slot(r.geometry)
-            if slot is None:
-                still.append(r)
-                continue
-            r.slot = slot
-            r.admitted = now
-            r.next_n = self.chunk
-            self.active.append(r)
-        self.pending = still
-        self.stats.max_active = max(self.stats.max_active, len(self.active))
-
-    def _round(self, clock):
-        chosen = select_round(self.active, self.round_budget)
-        jobs = [(r.slot, r.source, r.histories, r.next_n, self.seed_base + r.rid) for r in chosen]
-        dpm.dpm_run_batch(self.d.ctx, jobs, dpm.run_opts(n_batches=self.n_batches))
-        res = dpm.dpm_dmax_sigma(self.d.ctx, [r.slot for r in chosen])
-        # the round's device status (raises on a queue overflow or a timed-out
-        # wait) and release of its timing events
-        st = dpm.dpm_batch_stats(self.d.ctx)
-        self.stats.gpu_ms += st["transport_ms"]
-        now = clock()
-        self.stats.rounds += 1
-        done_ids = set()
-        for r, (dose, sig, vox) in zip(chosen, res):
-            r.rounds += 1
-            r.histories += r.next_n
-            self.stats.histories += r.next_n
-            r.dose_max = dose
-            r.rel_sigma = sig / dose if dose > 0 else math.inf
-            r.next_n = self._next_chunk(r)
-            if r.rel_sigma <= self.target:
+            if r.admitted is None:
+                r.admitted = admitted_by
+            r.slot, r.histories, r.rounds = st["slot"], st["histories"], st["rounds"]
+            r.rel_sigma, r.dose_max = st["rel_sigma"], st["dose_max"]
+            if st["state"] == dpm.REQ_DONE:
                 r.done = now
                 if self.keep:
-                    r.raw = dpm.dpm_read_dose(self.d.ctx, r.slot, self.geoms[r.geometry].n_vox, False, False, True)[2]
-                self._release(r.slot)
+                    n_vox = self.geoms[r.geometry].n_vox
+                    r.raw = dpm.dpm_read_dose(self.d.ctx, r.slot, n_vox, False, False, True)[2]
+                self.srv.release(rid)
                 r.slot = None
                 self.stats.completed.append(r)
-                done_ids.add(r.rid)
-        self.active = [r for r in self.active if r.rid not in done_ids]
-
-    def _next_chunk(self, r):
-        if not self.adaptive or not math.isfinite(r.rel_sigma) or r.rel_sigma <= 0:
-            return self.chunk
-        need = r.histories * (r.rel_sigma / self.target) ** 2 * self.overshoot - r.histories
-        return int(min(max(need, self.chunk), self.max_chunk))
+                del waiting[rid]
 
     def run(self, requests, clock=None, time_scale=1.0):
         """Serve `requests` (sorted by arrival, seconds from start) in real time
         (time_scale > 1 replays arrivals faster).  Returns ServeStats."""
         t0 = time.perf_counter()
         clock = clock or (lambda: (time.perf_counter() - t0) * time_scale)
+        base = self.srv.info()
         todo = sorted(requests, key=lambda r: r.arrival)
+        waiting = {}  # library request id -> Request
         i = 0
-        while i < len(todo) or self.pending or self.active:
+        while i < len(todo) or waiting:
             now = clock()
             while i < len(todo) and todo[i].arrival <= now:
-                self.submit(todo[i])
+                r = todo[i]
+                waiting[self.srv.submit(self.template[r.geometry], r.source, self.seed_base + r.rid)] = r
                 i += 1
-            self._admit(now)
-            if self.active:
-                self._round(clock)
-            elif i < len(todo):
+            if waiting:
+                before = self.srv.info()["n_rounds"]
+                self.srv.round()
+                info = self.srv.info()
+                if info["n_rounds"] == before and info["n_pending"]:
+                    # nothing active and still nothing admissible, with every
+                    # released slot free to go
+                    raise RuntimeError("a request does not fit the HBM budget")
+                self._collect(waiting, now, clock())
+            else:
                 time.sleep(max(0.0, (todo[i].arrival - clock()) / time_scale))
-            elif self.pending:
-                raise RuntimeError("a request does not fit the HBM budget")
+        info = self.srv.info()
         self.stats.wall = clock()
+        self.stats.rounds += info["n_rounds"] - base["n_rounds"]
+        self.stats.histories += info["histories"] - base["histories"]
+        self.stats.gpu_ms += info["gpu_ms"] - base["gpu_ms"]
+        self.stats.max_active = max(self.stats.max_active, info["max_active"])
+        self.stats.peak_bytes = max(self.stats.peak_bytes, self.fixed + info["peak_slot_bytes"])
         return self.stats
 
     def close(self):
+        if self.srv is not None:
+            self.srv.close()
+            self.srv = None
         self.d.close()
-
-
-def select_round(active, budget):
-    """The requests of the next round: oldest first (`active` is in arrival
-    order), each with its whole next chunk, while the chunks fit in `budget`
-    histories; a request that does not fit is passed over for younger ones
-    with smaller chunks.  The oldest request always runs."""
-    chosen, total = [], 0
-    for r in active:
-        if chosen and total + r.next_n > budget:
-            continue
-        chosen.append(r)
-        total += r.next_n
-    return chosen
 
 
 def poisson_requests(n, rate, n_geoms, seed=5, beamlet=0.5, geom_extent=None):

@@ -54,3 +54,33 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(dpm.dpm_run_opts) == 6 * 4 + 8 + 3 * 4 + 4
     assert ctypes.sizeof(dpm.dpm_job) == 4 + 4 + ctypes.sizeof(dpm.dpm_source) + 3 * 8
     assert ctypes.sizeof(dpm.dpm_run_stats) == 8 + 2 * 4 + 4 * 8 + 5 * 8 + 2 * 8 + 2 * 8
+
+
+ABI_STRUCTS = ["dpm_material", "dpm_table_params", "dpm_source", "dpm_run_opts", "dpm_run_stats", "dpm_job",
+               "dpm_serve_opts", "dpm_request_status", "dpm_server_info"]
+
+
+def test_struct_fields_match_the_c_compiler(tmp_path):
+    """Every binding struct against the header as gcc lays it out: the same
+    field names, offsets and total size."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dpm.h"', "int main(void) {"]
+    expect = []
+    for name in ABI_STRUCTS:
+        cls = getattr(dpm, name)
+        lines.append(f'  printf("%zu\\n", sizeof({name}));')
+        expect.append(ctypes.sizeof(cls))
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({name}, {field}));')
+            expect.append(getattr(cls, field).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True, capture_output=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
