@@ -36,7 +36,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--kernel", choices=["queue", "history"], default="queue")
+    ap.add_argument("--kernel", choices=["queue", "history", "paper_f32", "paper_cas"], default="queue",
+                    help="transport kernel; paper_*: one history per thread with the paper's float tally")
     ap.add_argument("--workload", default="6mv_wbw_61x61x60")
     ap.add_argument("--histories", type=int, default=0, help="histories per step (default: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -107,6 +108,11 @@ def measured_peaks():
             d = json.load(f)
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+# --kernel: (dpm_run_opts.kernel, the transport kernel's name)
+KERNELS = {"queue": (0, "k_queue"), "history": (1, "k_history"), "paper_f32": (2, "k_history_paper"),
+           "paper_cas": (3, "k_history_paper")}
 
 
 def profiled_traffic(kernel: str, workload: str, key: str = "traffic_bytes_per_history"):
@@ -287,7 +293,7 @@ def main():
     stream = torch.cuda.Stream()
     wl = W.WORKLOADS[args.workload]()
     n = args.histories or wl.n_histories
-    kernel = dpm.KERNEL_QUEUE if args.kernel == "queue" else dpm.KERNEL_HISTORY
+    kernel = KERNELS[args.kernel][0]
     ph = wl.phantom
     d = dpm.Dpm(local, W.MATERIALS, wl.params, stream=stream)
     pid = d.load_phantom(ph)
@@ -353,15 +359,16 @@ def main():
     sec_per_hist = st["n_pushed"] / n_tot
     bytes_per_hist = 8 * atom_per_hist + 88 * sec_per_hist + 44
     achieved = bytes_per_hist * hist_per_launch / t_kernel_s / 1e9
-    kname = "k_queue" if kernel == dpm.KERNEL_QUEUE else "k_history"
+    kname = KERNELS[args.kernel][1]
     tph = profiled_traffic(kname, args.workload)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": tph * hist_per_launch if tph else None, "peak_kind": peak_kind, "kernel": "k_queue" if kernel == dpm.KERNEL_QUEUE else "k_history",
+            "traffic": tph * hist_per_launch if tph else None, "peak_kind": peak_kind, "kernel": kname,
             "kernel_ms_per_launch": t_kernel_s * 1000, "bytes_per_history": bytes_per_hist,
             "tally_atomics_per_history": atom_per_hist, "secondaries_per_history": sec_per_hist,
             "kernel_share_of_step": st["transport_ms"] / max(tot_ms, 1e-9)}
 
-    launches_per_step = 3 if kernel == dpm.KERNEL_QUEUE else 2  # (queue init +) transport + fold
+    # queue init + transport + fold; transport + fold; transport + float rounding + fold
+    launches_per_step = {"queue": 3, "history": 2}.get(args.kernel, 3)
 
     line = {"metric": "histories/s", "value": value, "unit": "histories/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -87,10 +87,18 @@ typedef struct {
 } dpm_source;
 
 /* Kernel selection and launch shape.  Zero fields take defaults. */
-enum { DPM_KERNEL_QUEUE = 0, DPM_KERNEL_HISTORY = 1 };
+enum { DPM_KERNEL_QUEUE = 0, DPM_KERNEL_HISTORY = 1, DPM_KERNEL_PAPER_F32 = 2, DPM_KERNEL_PAPER_CAS = 3 };
 typedef struct {
-    int kernel;        /* DPM_KERNEL_QUEUE (persistent, particle queues) or
-                          DPM_KERNEL_HISTORY (one history per thread, private stack) */
+    int kernel;        /* DPM_KERNEL_QUEUE (persistent, particle queues);
+                          DPM_KERNEL_HISTORY (one history per thread, private stack);
+                          DPM_KERNEL_PAPER_F32 / _CAS: DPM_KERNEL_HISTORY with the paper's
+                          tally (Sec. 2.4) instead of the exact one, as an ablation: a
+                          sparse per-thread (voxel, energy) counter emptied at the end of
+                          each history into float slabs by atomic float adds (native, or
+                          a compare-and-swap loop), then rounded to the fixed-point tally.
+                          Same trajectories as the other kernels; the tally differs from
+                          theirs by float rounding and is not reproducible bit for bit.
+                          dpm_run only (DPM_EINVAL elsewhere or for other values). */
     int n_batches;     /* history batches for the sigma estimate (default 50, max 1024) */
     int block_size;    /* per-history kernel: threads per block (multiple of 32; 0 = 128).
                           The queue kernel always runs blocks of 128 threads (it schedules
@@ -325,7 +333,10 @@ int dpm_diag_table(dpm_ctx *ctx, int which, int mat, int n, const double *energy
 
 /* Run the device samplers on n uniforms u[i] (host) at energy e (MeV):
    which 0 KN eps, 1 Moller eps = W/T, 2 brems k (MeV), 3 pair eps,
-   4 MSC 1-mu for q = aux (mean of 1-mu), 5 6 MV spectrum energy. */
+   4 MSC 1-mu for q = aux (mean of 1-mu), 5 6 MV spectrum energy,
+   6 exponential path -ln(u) in mean free paths, 7 direction rotation: the
+   unit vector (0.36, -0.48, 0.8) (aux 0..2) or +z (aux 3..5) turned by polar
+   cosine e and azimuth 2 pi u, its component int(aux) % 3. */
 int dpm_diag_sample(dpm_ctx *ctx, int which, double e, double aux, int n, const double *u, double *out);
 
 /* n Philox4x32-10 blocks for counters ctr[4*i..] and keys key[2*i..] (host). */

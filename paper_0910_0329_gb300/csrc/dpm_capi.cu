@@ -78,6 +78,7 @@ void free_phantom(PhantomState *p) {
   cudaFree(p->d_rho);
   cudaFree(p->d_mumax);
   cudaFree(p->d_slabs);
+  cudaFree(p->d_fslabs);
   cudaFree(p->d_S1);
   cudaFree(p->d_Q);
   cudaFree(p->d_counters);
@@ -370,6 +371,8 @@ int dpm_build_tables(dpm_ctx *c, const dpm_material *mats, int n_mat, const dpm_
   d.wcc = float(p->wcc);
   d.wcr = float(p->wcr);
   d.f_e = float(p->f_e);
+  d.x_fe = float(std::log1p(-p->f_e) * (t.n_e - 1) / (std::log(t.e_hi) - std::log(t.e_lo)));
+  d.x_eabs = float((std::log(p->eabs_e) - std::log(t.e_lo)) * (t.n_e - 1) / (std::log(t.e_hi) - std::log(t.e_lo)));
   c->dt = d;
   c->params = *p;
   c->tables_ready = true;
@@ -456,6 +459,8 @@ int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t 
   if (!p) return fail(c, DPM_EINVAL, "bad phantom id");
   dpm_run_opts o{};
   if (opts) o = *opts;
+  if (o.kernel < DPM_KERNEL_QUEUE || o.kernel > DPM_KERNEL_PAPER_CAS) return fail(c, DPM_EINVAL, "unknown kernel");
+  const bool paper = o.kernel == DPM_KERNEL_PAPER_F32 || o.kernel == DPM_KERNEL_PAPER_CAS;
   RunParams R{};
   int rc = ctx_run_params(c, p, src, first, n, seed, o.physics_flags, R);
   if (rc) return rc;
@@ -464,7 +469,15 @@ int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t 
   uint64_t bs = 0;
   int B = 0;
   if ((rc = ctx_prepare_batches(c, p, n, o.n_batches, bs, B))) return rc;
-  CUDA_TRY(c, cudaMemsetAsync(p->d_slabs, 0, size_t(B) * p->V * sizeof(unsigned long long), c->stream));
+  if (paper && p->fslab_batches < size_t(B)) {
+    cudaFree(p->d_fslabs);
+    p->d_fslabs = nullptr;
+    p->fslab_batches = 0;
+    if ((rc = dalloc(c, &p->d_fslabs, size_t(B) * p->V))) return rc;
+    p->fslab_batches = size_t(B);
+  }
+  if (paper) CUDA_TRY(c, cudaMemsetAsync(p->d_fslabs, 0, size_t(B) * p->V * sizeof(float), c->stream));
+  else CUDA_TRY(c, cudaMemsetAsync(p->d_slabs, 0, size_t(B) * p->V * sizeof(unsigned long long), c->stream));
   R.n_batches = B;
   R.slabs = p->d_slabs;
   R.counters = p->d_counters;
@@ -477,6 +490,11 @@ int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t 
   if (o.kernel == DPM_KERNEL_HISTORY) {
     CUDA_TRY(c, cudaEventRecord(ev[0], c->stream));
     launch_history(R, bs, c->sm_count, o.block_size, c->stream);
+  } else if (paper) {
+    // the float slabs' rounding into the fixed-point slabs counts as transport
+    CUDA_TRY(c, cudaEventRecord(ev[0], c->stream));
+    launch_history_paper(R, bs, o.kernel == DPM_KERNEL_PAPER_CAS, p->d_fslabs, size_t(B) * p->V, c->sm_count,
+                         c->stream);
   } else {
     std::string qerr;
     int qrc = queue_run(c->queue, R, bs, o, c->sm_count, c->stream, ev[0], qerr);
@@ -662,7 +680,7 @@ int dpm_diag_table(dpm_ctx *c, int which, int mat, int n, const double *energy, 
 int dpm_diag_sample(dpm_ctx *c, int which, double e, double aux, int n, const double *u, double *out) {
   if (!c) return DPM_EINVAL;
   if (!c->tables_ready) return fail(c, DPM_ESTATE, "no tables");
-  if (n < 0 || (n > 0 && (!u || !out)) || which < 0 || which > 5) return fail(c, DPM_EINVAL, "bad arguments");
+  if (n < 0 || (n > 0 && (!u || !out)) || which < 0 || which > 7) return fail(c, DPM_EINVAL, "bad arguments");
   if (n == 0) return DPM_OK;
   cudaSetDevice(c->device);
   double *d = nullptr;

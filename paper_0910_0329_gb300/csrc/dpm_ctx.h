@@ -34,6 +34,8 @@ struct PhantomState {
   double rho_max[DPM_MAX_MAT] = {0};
   unsigned long long *d_slabs = nullptr;
   size_t slab_batches = 0;
+  float *d_fslabs = nullptr;  // float slabs of the paper's tally (ablation kernels only)
+  size_t fslab_batches = 0;
   long long *d_S1 = nullptr;
   double *d_Q = nullptr;
   unsigned long long *d_counters = nullptr;

@@ -59,6 +59,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // uniform in the open interval (0, 1) from the top 24 bits
 __device__ __forceinline__ float u01(uint32_t x) { return (float(x >> 8) + 0.5f) * (1.0f / 16777216.0f); }
 
+// -ln(u) for an exponential free path, with the hardware logarithm (absolute
+// error about 2^-21 near u = 1, far below the paths' statistical spread); the
+// clamp keeps a rounding just above zero from reversing a flight.
+__device__ __forceinline__ float neglog(float u) { return fmaxf(-__logf(u), 0.f); }
+
 // ---------------------------------------------------------------------------
 // Particle state.  (ix, iy, iz) are tracked exactly across voxel faces.
 // ---------------------------------------------------------------------------
@@ -161,13 +166,15 @@ __device__ __forceinline__ void locate(Part &p, const DevPhantom &P) {
   p.iz = min(max(int(floorf(p.z / P.dz)), 0), P.nz - 1);
 }
 
-// Rotate the direction by polar cosine c and azimuth pi*h (h in half turns,
-// so that sincospif's exact argument reduction applies).
+// Rotate the direction by polar cosine c and azimuth pi*h (h in half turns).
+// h is reduced modulo 2 to [-1, 1), where the hardware sine and cosine are
+// accurate to about 2^-21 absolute; the direction is renormalised below.
 __device__ __forceinline__ void rotate(float &u, float &v, float &w, float c, float h) {
   c = fminf(fmaxf(c, -1.f), 1.f);
   const float s = sqrtf(fmaxf(0.f, 1.f - c * c));
   float sp, cp;
-  sincospif(h, &sp, &cp);
+  const float t = h - 2.f * floorf(0.5f * h + 0.5f);  // h modulo 2, in [-1, 1)
+  __sincosf(3.14159265f * t, &sp, &cp);
   const float r2 = u * u + v * v;
   float nu, nv, nw;
   if (r2 < 1e-10f) {
@@ -193,6 +200,15 @@ struct EIdx {
   int i;
   float f;
 };
+
+// Grid position x (fractional node index) clamped to the table.
+__device__ __forceinline__ EIdx eidx_x(const DevTables &T, float x) {
+  x = fminf(fmaxf(x, 0.f), float(T.n_e - 1) - 1e-3f);
+  EIdx e;
+  e.i = int(x);
+  e.f = x - float(e.i);
+  return e;
+}
 
 __device__ __forceinline__ EIdx eidx(const DevTables &T, float E) {
   float x = (logf(E) - T.lnE_lo) * T.inv_dlnE;
@@ -459,7 +475,7 @@ __device__ bool photon_segment(Part &p, const Ctx &R, Sink &s, int max_draws = k
     for (int j = 0; j < 2; ++j) {
       const float us = u01(j ? r.z : r.x), ua = u01(j ? r.w : r.y);
       s.count_flight();
-      move(p, -logf(us) * inv_mumax);
+      move(p, neglog(us) * inv_mumax);
       if (!(p.x >= 0.f && p.x < X && p.y >= 0.f && p.y < Y && p.z >= 0.f && p.z < Z)) {
         s.escape(p.E);
         return false;
@@ -533,12 +549,16 @@ __device__ bool electron_step(Part &p, const Ctx &R, Sink &s) {
   const int m = P.mat[v];
   const float rho = P.rho[v];
   const float T0 = p.E;
-  const float4 r0 = el_at(T, m, eidx(T, T0));  // R, S, Sigma_hard, 1/lambda1
+  // on the ln(E) grid the step's end energy (1 - f_e) T0, or eabs_e, lies a
+  // fixed shift below T0's position: one logarithm serves both lookups
+  float x0 = (logf(T0) - T.lnE_lo) * T.inv_dlnE;
+  const float xe = fmaxf(x0 + T.x_fe, T.x_eabs);
   const float Tend = fmaxf((1.f - T.f_e) * T0, T.eabs_e);
-  const float Rend = el_at(T, m, eidx(T, Tend)).x;
+  const float4 r0 = el_at(T, m, eidx_x(T, x0));  // R, S, Sigma_hard, 1/lambda1
+  const float Rend = el_at(T, m, eidx_x(T, xe)).x;
   const float sE = fmaxf(r0.x - Rend, 0.f) / rho;
   const uint4 rn = draw(p, R);
-  const float sh = (r0.z > 0.f && !(T.flags & DPM_NO_HARD)) ? -logf(u01(rn.x)) / (rho * r0.z) : kInf;
+  const float sh = (r0.z > 0.f && !(T.flags & DPM_NO_HARD)) ? neglog(u01(rn.x)) / (rho * r0.z) : kInf;
   const bool hard = sh < sE;
   const float st = hard ? sh : sE;
   const float tau = u01(rn.y);

@@ -69,6 +69,21 @@ __global__ void k_diag_sample(DevTables T, int which, float e, float aux, int n,
       break;
     }
     case 5: r = spectrum_6mv(x); break;
+    case 6: r = neglog(x); break;
+    case 7: {
+      // rotation by polar cosine e and azimuth pi * 2x of an oblique unit
+      // direction (aux 0..2) or of +z (aux 3..5); component int(aux) % 3
+      const int a = int(aux);
+      float du = 0.f, dv = 0.f, dw = 1.f;
+      if (a < 3) {
+        du = 0.36f;
+        dv = -0.48f;
+        dw = 0.8f;
+      }
+      rotate(du, dv, dw, e, 2.f * x);
+      r = (a % 3 == 0) ? du : (a % 3 == 1) ? dv : dw;
+      break;
+    }
     default: r = 0.0;
   }
   out[i] = r;

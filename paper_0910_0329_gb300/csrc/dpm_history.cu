@@ -131,6 +131,159 @@ void launch_history(const RunParams &R, uint64_t batch_size, int sm_count, int b
   k_history<<<grid > 0 ? grid : 1, block, 0, st>>>(R, batch_size);
 }
 
+// ---------------------------------------------------------------------------
+// The paper's own tally (Sec. 2.4), kept as an ablation of the exact one above.
+// Each thread holds a sparse dose counter of kPaperCounter (voxel, energy)
+// entries in its own memory: a deposit adds to its voxel's entry (searched
+// from the newest, since consecutive deposits usually share a voxel) or opens
+// a new one.  When the history ends, or the counter is full, the entries are
+// added to a float dose array with atomic float additions.  kCas emulates the
+// float addition with a compare-and-swap loop on the 32-bit word, the scheme
+// the paper uses on a GPU without float atomics; otherwise the native float
+// atomic add is used.  Float sums depend on the order of the additions, so
+// this tally is not reproducible bit for bit; k_f32_to_fixed rounds it to
+// the fixed-point slabs for the common fold.
+// ---------------------------------------------------------------------------
+constexpr int kPaperCounter = 128;
+constexpr int kCasTries = 1 << 20;  // a bound on one CAS addition's retries
+
+template <bool kCas>
+__device__ __forceinline__ bool add_f32(float *a, float x) {
+  if (!kCas) {
+    atomicAdd(a, x);
+    return true;
+  }
+  unsigned int *w = reinterpret_cast<unsigned int *>(a);
+  unsigned int old = *w;
+  for (int t = 0; t < kCasTries; ++t) {
+    const unsigned int seen = old;
+    old = atomicCAS(w, seen, __float_as_uint(__uint_as_float(seen) + x));
+    if (old == seen) return true;
+  }
+  return false;
+}
+
+template <bool kCas>
+struct PaperSink {
+  const RunParams &R;
+  float *fslab = nullptr;
+  int n = 0;
+  int lv[kPaperCounter];
+  float le[kPaperCounter];
+  long long cnt[C_N];
+  int err = 0;
+  Part *stack;
+  int sp = 0, cap;
+
+  __device__ PaperSink(const RunParams &r, Part *st, int c) : R(r), stack(st), cap(c) {
+#pragma unroll
+    for (int i = 0; i < C_N; ++i) cnt[i] = 0;
+  }
+  __device__ void flush() {
+    for (int i = 0; i < n; ++i) {
+      if (!add_f32<kCas>(fslab + lv[i], le[i])) err |= ERR_TIMEOUT;
+    }
+    cnt[C_ATOM] += n;
+    n = 0;
+  }
+  __device__ void deposit(int v, float dE) {
+    for (int i = n - 1; i >= 0; --i) {
+      if (lv[i] == v) {
+        le[i] += dE;
+        return;
+      }
+    }
+    if (n == kPaperCounter) flush();
+    lv[n] = v;
+    le[n] = dE;
+    ++n;
+  }
+  // run counters exactly as HistSink keeps them, so that the energy balance
+  // of both tallies is the same
+  __device__ __forceinline__ void escape(float E) { cnt[C_ESC] += HistSink::fxc(E); }
+  __device__ __forceinline__ void push(const Part &q) {
+    ++cnt[C_PUSH];
+    if (sp < cap) {
+      stack[sp++] = q;
+    } else {
+      err |= ERR_OVERFLOW;
+      cnt[C_ESC] += HistSink::fxc(q.E + (q.type == POSITRON ? 2.f * kMc2f : 0.f));
+    }
+  }
+  __device__ __forceinline__ void error(int e) { err |= e; }
+  __device__ __forceinline__ void count_step() { ++cnt[C_ESTEP]; }
+  __device__ __forceinline__ void count_flight() { ++cnt[C_GFLIGHT]; }
+  __device__ __forceinline__ void count_interaction() { ++cnt[C_GINT]; }
+};
+
+template <bool kCas>
+__global__ void __launch_bounds__(128) k_history_paper(const __grid_constant__ RunParams R, uint64_t batch_size,
+                                                       float *fslabs) {
+  Part stack[kHistStack];
+  PaperSink<kCas> s(R, stack, kHistStack);
+  const size_t V = size_t(R.P.nx) * R.P.ny * R.P.nz;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t hl = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; hl < R.n; hl += stride) {
+    s.fslab = fslabs + (hl / batch_size) * V;
+    Part p;
+    const bool hit = make_primary(p, R, uint32_t(hl));
+    s.cnt[C_EMIT] += HistSink::fxc(p.E);
+    if (!hit) {
+      s.cnt[C_MISS] += HistSink::fxc(p.E);
+      continue;
+    }
+    s.sp = 0;
+    s.stack[s.sp++] = p;
+    while (s.sp > 0) {
+      Part q = s.stack[--s.sp];
+      if (q.type == PHOTON) {
+        int g = 0;
+        while (photon_segment(q, R, s)) {
+          if (++g >= kMaxPhotonSegments) {
+            s.error(ERR_STEPCAP);
+            s.deposit(vox(q, R.P), q.E);
+            break;
+          }
+        }
+      } else {
+        int n = 0;
+        while (electron_step(q, R, s)) {
+          if (++n >= kMaxElectronSteps) {
+            s.error(ERR_STEPCAP);
+            s.deposit(vox(q, R.P), q.E);
+            break;
+          }
+        }
+      }
+    }
+    s.flush();
+  }
+  reduce_counters(s.cnt, s.err, R);
+}
+
+// Float dose slabs to the fixed-point slabs (nearest multiple of 2^-32 MeV).
+__global__ void k_f32_to_fixed(const float *f, unsigned long long *slabs, size_t n) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    slabs[i] = (unsigned long long)__double2ll_rn(double(f[i]) * 4294967296.0);
+}
+
+void launch_history_paper(const RunParams &R, uint64_t batch_size, bool cas, float *fslabs, size_t n_slab,
+                          int sm_count, cudaStream_t st) {
+  const int block = 128;
+  const uint64_t need = (R.n + block - 1) / block;
+  const uint64_t cap = uint64_t(sm_count) * 16;
+  const int grid = int(need < cap ? need : cap);
+  if (cas) {
+    cudaFuncSetAttribute(k_history_paper<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    k_history_paper<true><<<grid > 0 ? grid : 1, block, 0, st>>>(R, batch_size, fslabs);
+  } else {
+    cudaFuncSetAttribute(k_history_paper<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    k_history_paper<false><<<grid > 0 ? grid : 1, block, 0, st>>>(R, batch_size, fslabs);
+  }
+  const size_t cgrid = (n_slab + 255) / 256 < size_t(sm_count) * 8 ? (n_slab + 255) / 256 : size_t(sm_count) * 8;
+  k_f32_to_fixed<<<cgrid > 0 ? int(cgrid) : 1, 256, 0, st>>>(fslabs, R.slabs, n_slab);
+}
+
 // Sum the batch slabs of one run into S1 (exact int64) and Q = sum_b d_b^2/n_b.
 __global__ void k_fold(const unsigned long long *slabs, int nb, size_t V, const double *inv_nb, long long *S1,
                        double *Q) {

@@ -46,6 +46,7 @@ struct DevTables {
   float msc_x0, msc_inv_dx;
   float eabs_e, eabs_g, wcc, wcr, f_e;
   int flags;  // DPM_NO_HARD / DPM_NO_MSC
+  float x_fe, x_eabs;  // grid-index shift of an energy step (1 - f_e), grid index of eabs_e
 };
 
 struct DevPhantom {

@@ -8,6 +8,10 @@
 namespace dpm {
 
 void launch_history(const RunParams &R, uint64_t batch_size, int sm_count, int block, cudaStream_t st);
+// The paper's float tally (ablation): transport into float slabs (n_slab
+// floats, zeroed by the caller), then their rounding into R.slabs.
+void launch_history_paper(const RunParams &R, uint64_t batch_size, bool cas, float *fslabs, size_t n_slab,
+                          int sm_count, cudaStream_t st);
 void launch_fold(const unsigned long long *slabs, int nb, size_t V, const double *inv_nb, long long *S1, double *Q,
                  int sm_count, cudaStream_t st);
 void launch_normalize(const long long *S1, const double *Q, const float *rho, size_t V, double n, double B,

@@ -118,8 +118,6 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
   return *(const volatile unsigned long long *)p;
 }
 
-__device__ __forceinline__ uint32_t ld_volatile32(const uint32_t *p) { return *(const volatile uint32_t *)p; }
-
 // Slot sequence words: the producer publishes a record and the consumer
 // frees its slot with a release store; both wait for the word with acquire
 // loads, so the record's plain loads and stores are ordered around them.
