@@ -59,6 +59,9 @@ typedef struct {
     int n_elem;
     double Z[DPM_MAX_ELEM], A[DPM_MAX_ELEM], w[DPM_MAX_ELEM];
     double i_ev;
+    double rho_de;  /* g/cm^3 at which the Sternheimer-Peierls density-effect
+                       correction of the collision stopping power is evaluated
+                       (the material's nominal density); 0 = no density effect */
 } dpm_material;
 
 /* Transport and table parameters (Sec. 3 absorption energies; the cuts and

@@ -258,18 +258,57 @@ double or_mu_pair(const or_material *m, double E) {
 /* Electrons                                                                */
 /* ======================================================================= */
 
-/* Restricted collision stopping power (Bethe, electrons, no density effect),
-   MeV cm^2/g, for energy transfers below d = min(wcc, T/2):
+/* Plasma energy hbar*omega_p = hbar c sqrt(4 pi n_e r_e) of the material at
+   its density-effect density, in eV (n_e electrons per cm^3). */
+double or_plasma_energy_ev(const or_material *m) {
+    const double HBARC = 1.973269804e-11; /* MeV cm */
+    double ne = m->rho_de * NAV * mat_z_over_a(m);
+    return HBARC * sqrt(4.0 * PI * ne * RE) * 1e6;
+}
+
+/* Density-effect correction delta of the collision stopping power, by the
+   general formula of Sternheimer and Peierls (1971) for condensed media,
+   in X = log10(beta gamma) = log10(p/mc):
+     Cbar = 2 ln(I / hbar omega_p) + 1;
+     I < 100 eV:  X1 = 2, X0 = 0.2 if Cbar < 3.681 else 0.326 Cbar - 1.0;
+     I >= 100 eV: X1 = 3, X0 = 0.2 if Cbar < 5.215 else 0.326 Cbar - 1.5;
+     delta = 0 below X0; 2 ln10 X - Cbar + a (X1 - X)^3 on [X0, X1) with a
+     making delta vanish at X0; 2 ln10 X - Cbar from X1 on.
+   Zero when the material has no density-effect density. */
+double or_density_delta(const or_material *m, double T) {
+    if (!(m->rho_de > 0.0)) return 0.0;
+    double cbar = 2.0 * log(m->i_ev / or_plasma_energy_ev(m)) + 1.0;
+    double x0, x1;
+    if (m->i_ev < 100.0) {
+        x1 = 2.0;
+        x0 = cbar < 3.681 ? 0.2 : 0.326 * cbar - 1.0;
+    } else {
+        x1 = 3.0;
+        x0 = cbar < 5.215 ? 0.2 : 0.326 * cbar - 1.5;
+    }
+    double two_ln10 = 2.0 * log(10.0);
+    double t = T / MC2;
+    double X = 0.5 * log10(t * (t + 2.0)); /* (beta gamma)^2 = t (t + 2) */
+    if (X < x0) return 0.0;
+    double lin = two_ln10 * X - cbar;
+    if (X >= x1) return lin;
+    double a = (cbar - two_ln10 * x0) / ((x1 - x0) * (x1 - x0) * (x1 - x0));
+    return lin + a * (x1 - X) * (x1 - X) * (x1 - X);
+}
+
+/* Restricted collision stopping power (Bethe, electrons), MeV cm^2/g, for
+   energy transfers below d = min(wcc, T/2):
    2 pi re^2 mc^2 N_A (Z/A)/beta^2 [ ln(2(t+2)/(I/mc^2)^2) - 1 - beta^2
-       + ln((t-d)d) + t/(t-d) + (d^2/2 + (2t+1) ln(1-d/t))/gamma^2 ],
-   t = T/mc^2, d in units of mc^2.  With d = t/2 this is the unrestricted form. */
+       + ln((t-d)d) + t/(t-d) + (d^2/2 + (2t+1) ln(1-d/t))/gamma^2 - delta ],
+   t = T/mc^2, d in units of mc^2, delta the density effect (zero unless the
+   material asks for it).  With d = t/2 this is the unrestricted form. */
 double or_scol(const or_material *m, double T, double wcc) {
     double t = T / MC2, g = t + 1.0, b2 = 1.0 - 1.0 / (g * g);
     double I = m->i_ev * 1e-6 / MC2;
     double d = wcc / MC2;
     if (d > 0.5 * t) d = 0.5 * t;
     double br = log(2.0 * (t + 2.0) / (I * I)) - 1.0 - b2 + log((t - d) * d) + t / (t - d)
-                + (0.5 * d * d + (2.0 * t + 1.0) * log(1.0 - d / t)) / (g * g);
+                + (0.5 * d * d + (2.0 * t + 1.0) * log(1.0 - d / t)) / (g * g) - or_density_delta(m, T);
     return 2.0 * PI * RE * RE * MC2 * NAV * mat_z_over_a(m) / b2 * br;
 }
 

@@ -13,7 +13,8 @@
  *             Bethe-Heitler pair production; ray-marched voxel by voxel with
  *             the real attenuation (no Woodcock majorant);
  *   electrons condensed history: CSDA with the Bethe restricted collision
- *             stopping power (I per material, no density effect) plus the
+ *             stopping power (I per material; optionally with the
+ *             Sternheimer-Peierls density effect) plus the
  *             restricted bremsstrahlung loss, random-hinge screened-Rutherford
  *             multiple scattering, hard Moller collisions and hard
  *             bremsstrahlung by delta scattering (Sec. 2.1);
@@ -37,6 +38,7 @@ typedef struct {
     int n_elem;
     double Z[OR_MAX_ELEM], A[OR_MAX_ELEM], w[OR_MAX_ELEM];
     double i_ev;
+    double rho_de;  /* density (g/cm^3) of the density-effect correction; 0: none */
 } or_material;
 
 enum { OR_NO_HARD = 1, OR_NO_MSC = 2, OR_NO_SECONDARY_PHOTONS = 4 };
@@ -96,6 +98,8 @@ double or_gl_integrate_test(int which, double a, double b);
 /* electrons: stopping powers (MeV cm^2/g), hard cross sections (cm^2/g) --- */
 double or_x0(const or_material *m);
 double or_scol(const or_material *m, double T, double wcc);
+double or_plasma_energy_ev(const or_material *m);
+double or_density_delta(const or_material *m, double T);
 double or_srad(const or_material *m, double T, double wcr);
 double or_moller_sigma(const or_material *m, double T, double wcc);
 double or_moller_dsdw(const or_material *m, double T, double W);

@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
 
 class Material(C.Structure):
     _fields_ = [("n_elem", C.c_int), ("Z", C.c_double * 8), ("A", C.c_double * 8), ("w", C.c_double * 8),
-                ("i_ev", C.c_double)]
+                ("i_ev", C.c_double), ("rho_de", C.c_double)]
 
 
 class Params(C.Structure):
@@ -83,6 +83,7 @@ def lib():
                            ("or_mu_compton", [pm, d]), ("or_mu_photo", [pm, d, d]), ("or_mu_pair", [pm, d]),
                            ("or_pair_integral", [d, d, d, i]), ("or_pair_dsde_shape", [d, d, i]),
                            ("or_gl_integrate_test", [i, d, d]), ("or_x0", [pm]), ("or_scol", [pm, d, d]),
+                           ("or_plasma_energy_ev", [pm]), ("or_density_delta", [pm, d]),
                            ("or_srad", [pm, d, d]), ("or_moller_sigma", [pm, d, d]), ("or_moller_dsdw", [pm, d, d]),
                            ("or_brems_sigma", [pm, d, d]), ("or_brems_dsdk", [pm, d, d]),
                            ("or_lambda1_inv", [pm, d]), ("or_csda_path", [pm, C.POINTER(Params), d, d]),
@@ -114,6 +115,7 @@ def material(md: dict) -> Material:
     for k, (Z, A, w) in enumerate(els):
         m.Z[k], m.A[k], m.w[k] = Z, A, w
     m.i_ev = md["i_ev"]
+    m.rho_de = md.get("rho_de", 0.0)
     return m
 
 

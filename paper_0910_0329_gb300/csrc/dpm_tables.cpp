@@ -10,8 +10,9 @@
 //   photons   Klein-Nishina (free electrons); photoelectric c_pe sum(wZ^4/A)/E^3;
 //             unscreened extreme-relativistic Bethe-Heitler pair production
 //             with the logarithm clamped at zero;
-//   electrons Bethe restricted collision stopping power (ICRU 37 form, no
-//             density effect) + restricted radiative loss of the simplified
+//   electrons Bethe restricted collision stopping power (ICRU 37 form; with
+//             the Sternheimer-Peierls density effect for a material that
+//             gives a density for it) + restricted radiative loss of the simplified
 //             Bethe-Heitler spectrum (1/(X0 k))(4/3 - 4/3 y + y^2), X0 from
 //             Dahl's fit; hard Moller and bremsstrahlung cross sections;
 //             screened-Rutherford transport mean free path with Moliere
@@ -35,6 +36,9 @@ struct MatModel {
   double pair_weight;       // N_A sum(w Z(Z+1)/A)
   double inv_x0;            // 1/X0 in cm^2/g
   double ln_i2;             // ln((I/mc^2)^2)
+  // density effect: delta(X) over X = log10(beta gamma) (de_on false: none)
+  bool de_on;
+  double de_cbar, de_x0, de_x1, de_a;
   int n;
   double atoms_per_g[DPM_MAX_ELEM], Z[DPM_MAX_ELEM];
 
@@ -54,6 +58,31 @@ struct MatModel {
     }
     double i_mc2 = m.i_ev * 1e-6 / kMc2;
     ln_i2 = 2.0 * std::log(i_mc2);
+    // Sternheimer-Peierls general parameters for a condensed medium: the
+    // plasma energy 28.816 sqrt(rho Z/A) eV sets Cbar = 2 ln(I/hw_p) + 1; X0
+    // and X1 follow from Cbar and I; a joins the cubic to zero at X0
+    de_on = m.rho_de > 0.0;
+    de_cbar = de_x0 = de_x1 = de_a = 0.0;
+    if (de_on) {
+      const double hw_p = 28.816 * std::sqrt(m.rho_de * electrons_per_g / kNa);
+      de_cbar = 2.0 * std::log(m.i_ev / hw_p) + 1.0;
+      if (m.i_ev < 100.0) {
+        de_x1 = 2.0;
+        de_x0 = de_cbar < 3.681 ? 0.2 : 0.326 * de_cbar - 1.0;
+      } else {
+        de_x1 = 3.0;
+        de_x0 = de_cbar < 5.215 ? 0.2 : 0.326 * de_cbar - 1.5;
+      }
+      de_a = (de_cbar - 2.0 * std::log(10.0) * de_x0) / std::pow(de_x1 - de_x0, 3.0);
+    }
+  }
+  // delta at (beta gamma)^2 = bg2
+  double density_delta(double bg2) const {
+    if (!de_on) return 0.0;
+    const double x = 0.5 * std::log10(bg2);
+    if (x < de_x0) return 0.0;
+    const double d = 2.0 * std::log(10.0) * x - de_cbar;
+    return x < de_x1 ? d + de_a * std::pow(de_x1 - x, 3.0) : d;
   }
 };
 
@@ -123,7 +152,7 @@ double s_collision(const MatModel &m, double T, double wcc) {
   double d = std::min(wcc / kMc2, 0.5 * k.tau);
   double F = -1.0 - k.beta2 + std::log((k.tau - d) * d) + k.tau / (k.tau - d) +
              (0.5 * d * d + (2.0 * k.tau + 1.0) * std::log(1.0 - d / k.tau)) / (k.gam * k.gam);
-  double B = std::log(2.0 * (k.tau + 2.0)) - m.ln_i2 + F;
+  double B = std::log(2.0 * (k.tau + 2.0)) - m.ln_i2 + F - m.density_delta(k.bg2);
   return 2.0 * kPi * kRe * kRe * kMc2 * m.electrons_per_g / k.beta2 * B;
 }
 
@@ -207,7 +236,8 @@ bool build_tables(const dpm_material *mats, int n_mat, const dpm_table_params &p
   }
   if (!(p.e_max > 2.0 * std::max(p.eabs_e, p.eabs_g))) { err = "e_max too small"; return false; }
   for (int m = 0; m < n_mat; ++m) {
-    if (mats[m].n_elem < 1 || mats[m].n_elem > DPM_MAX_ELEM || !(mats[m].i_ev > 0)) {
+    if (mats[m].n_elem < 1 || mats[m].n_elem > DPM_MAX_ELEM || !(mats[m].i_ev > 0) ||
+        !(mats[m].rho_de >= 0 && std::isfinite(mats[m].rho_de))) {
       err = "invalid material " + std::to_string(m);
       return false;
     }

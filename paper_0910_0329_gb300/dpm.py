@@ -33,7 +33,7 @@ class DpmError(RuntimeError):
 
 class dpm_material(C.Structure):
     _fields_ = [("n_elem", C.c_int), ("Z", C.c_double * 8), ("A", C.c_double * 8), ("w", C.c_double * 8),
-                ("i_ev", C.c_double)]
+                ("i_ev", C.c_double), ("rho_de", C.c_double)]
 
 
 class dpm_table_params(C.Structure):
@@ -220,6 +220,7 @@ def material_struct(md: dict) -> dpm_material:
     for k, (Z, A, w) in enumerate(md["elements"]):
         m.Z[k], m.A[k], m.w[k] = Z, A, w
     m.i_ev = md["i_ev"]
+    m.rho_de = md.get("rho_de", 0.0)
     return m
 
 
@@ -493,6 +494,12 @@ class HostTables:
         if self.h:
             lib().dpm_host_tables_free(self.h)
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:

@@ -48,7 +48,7 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
 
 def test_struct_layouts_match_header():
     # sizes of the ABI structs as laid out by the C compiler (x86-64 / aarch64 LP64)
-    assert ctypes.sizeof(dpm.dpm_material) == 4 + 4 + 3 * 8 * 8 + 8
+    assert ctypes.sizeof(dpm.dpm_material) == 4 + 4 + 3 * 8 * 8 + 8 + 8
     assert ctypes.sizeof(dpm.dpm_table_params) == 7 * 8 + 8
     assert ctypes.sizeof(dpm.dpm_source) == 8 + 8 + 3 * 8 + 4 * 8
     assert ctypes.sizeof(dpm.dpm_run_opts) == 6 * 4 + 8 + 3 * 4 + 4

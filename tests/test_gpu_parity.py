@@ -247,3 +247,44 @@ def test_zero_width_pencil(kernel):
     print(r)
     assert r["n_vox"] > 100 and r["pass_frac"] >= 0.9, r
     assert abs(r["e_rel_diff"]) < max(0.2e-2, 3 * r["e_rel_sigma"]), r
+
+
+MATERIALS_DE = [dict(W.WATER, rho_de=1.0), dict(W.LUNG, rho_de=0.3), dict(W.BONE, rho_de=1.85)]
+
+
+def r50(dose, ph):
+    """Depth (cm) where the central-axis depth dose, past its maximum, falls
+    to half of it (central 3 x 3 columns, linear interpolation)."""
+    d = dose.reshape(ph.nz, ph.ny, ph.nx)
+    cy, cx = ph.ny // 2, ph.nx // 2
+    dd = d[:, cy - 1:cy + 2, cx - 1:cx + 2].mean(axis=(1, 2))
+    k = int(np.argmax(dd))
+    half = 0.5 * dd[k]
+    for j in range(k, ph.nz - 1):
+        if dd[j + 1] < half <= dd[j]:
+            f = (dd[j] - half) / (dd[j] - dd[j + 1])
+            return (j + 0.5 + f) * ph.dz
+    return ph.nz * ph.dz
+
+
+def test_density_effect_parity():
+    """20 MeV electrons on the water/lung/water slabs with the density-effect
+    correction (each material at its nominal density): GPU against the
+    oracle with the same materials, and the correction's lower stopping power
+    pushes the distal fall-off deeper than without it."""
+    wl = W.c0_electron_wlw()
+    orc = O.run(wl.phantom, MATERIALS_DE, wl.params, wl.source, 80000, 1000 + wl.seed, workers=WORKERS)
+    n_g = 800_000
+    with dpm.Dpm(0, MATERIALS_DE, wl.params) as d:
+        pid = d.load_phantom(wl.phantom)
+        d.run(pid, wl.source, n_g, wl.seed, n_batches=50)
+        dose, sigma, raw, st = d.read(pid)
+    assert st["error_flags"] == 0
+    r = compare(wl.phantom, dose, sigma, raw, n_g, orc)
+    print("density effect", r)
+    assert r["pass_frac"] >= 0.95 and abs(r["z_mean"]) < 0.15 and 0.8 < r["z_std"] < 1.2, r
+    assert abs(r["e_rel_diff"]) < 0.2e-2, r
+    dose0 = gpu_run(wl, n_g, dpm.KERNEL_QUEUE)[0]
+    shift = r50(dose, wl.phantom) - r50(dose0, wl.phantom)
+    print("R50 shift (cm)", shift)
+    assert shift > 0.2

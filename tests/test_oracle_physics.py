@@ -335,3 +335,72 @@ def test_ranecu_matches_direct_modular_arithmetic():
         assert u[i] == pytest.approx(z / m1, rel=1e-15)
     assert (e1, e2) == (x1, x2)
     assert stats.kstest(u, "uniform").pvalue > 0.01
+
+
+# --------------------------------------------------------------------------
+# density effect (Sternheimer-Peierls general formula; off unless a material
+# gives a density-effect density)
+# --------------------------------------------------------------------------
+def with_de(md, rho, **kw):
+    d = dict(md, rho_de=rho)
+    d.update(kw)
+    return M(d)
+
+
+def log10_bg(T):
+    t = T / MC2
+    return 0.5 * math.log10(t * (t + 2.0))
+
+
+def test_plasma_energy_and_cbar_of_water(L):
+    # tabulated for liquid water (Sternheimer, Berger and Seltzer 1984):
+    # hbar omega_p = 21.469 eV, -C = 3.5017 (with I = 75 eV)
+    w = with_de(W.WATER, 1.0)
+    assert L.or_plasma_energy_ev(w) == pytest.approx(21.469, abs=0.002)
+    T = 1e4  # far on the linear branch: delta = 2 ln10 X - Cbar
+    assert 2 * math.log(10) * log10_bg(T) - L.or_density_delta(w, T) == pytest.approx(3.5017, abs=2e-4)
+
+
+def test_density_effect_branches_join(L):
+    w = with_de(W.WATER, 1.0)
+    # below X0 = 0.2 (beta gamma < 10^0.2, T < 0.445 MeV) there is no correction
+    assert L.or_density_delta(w, 0.44) == 0.0 and L.or_density_delta(w, 0.45) > 0.0
+    assert L.or_density_delta(WATER, 20.0) == 0.0  # no density-effect density: none
+    t_of = lambda X: MC2 * (math.sqrt(1.0 + 10 ** (2 * X)) - 1.0)
+    for X in (0.2, 2.0):  # X0 and X1 of water (Cbar < 3.681, I < 100 eV)
+        lo, hi = L.or_density_delta(w, t_of(X - 1e-9)), L.or_density_delta(w, t_of(X + 1e-9))
+        assert lo == pytest.approx(hi, abs=1e-7)
+    # the cubic's slope matches the linear branch at X1
+    e = 1e-4
+    slope = (L.or_density_delta(w, t_of(2.0)) - L.or_density_delta(w, t_of(2.0 - e))) / e
+    assert slope == pytest.approx(2 * math.log(10), rel=1e-3)
+
+
+def test_fermi_plateau_does_not_depend_on_the_excitation_energy(L):
+    # far above X1 the -ln I^2 of the Bethe bracket cancels against delta's
+    # 2 ln I: the collision stopping power depends on the electron density only
+    T = 1e4
+    a = L.or_scol(with_de(W.WATER, 1.0), T, PARAMS["wcc"])
+    b = L.or_scol(with_de(W.WATER, 1.0, i_ev=150.0), T, PARAMS["wcc"])
+    assert a == pytest.approx(b, rel=1e-12)
+    # and without the density effect they differ by the ln I term
+    a0, b0 = L.or_scol(WATER, T, PARAMS["wcc"]), L.or_scol(M(dict(W.WATER, i_ev=150.0)), T, PARAMS["wcc"])
+    assert a0 / b0 - 1 > 0.03
+
+
+def test_density_effect_scales_with_density_on_the_plateau(L):
+    # hbar omega_p grows as sqrt(rho): Cbar, and so delta on the linear branch,
+    # shifts by ln(rho1/rho2)
+    T = 1e4
+    d1, d03 = L.or_density_delta(with_de(W.WATER, 1.0), T), L.or_density_delta(with_de(W.WATER, 0.3), T)
+    assert d1 - d03 == pytest.approx(math.log(1.0 / 0.3), rel=1e-12)
+
+
+def test_water_collision_stopping_power_with_density_effect_textbook(L):
+    # ESTAR (fitted Sternheimer parameters), liquid water: 1.849 MeV cm^2/g at
+    # 1 MeV and 1.968 at 10 MeV; the general formula's delta is a little lower
+    # than the fitted one at 10 MeV
+    w = with_de(W.WATER, 1.0)
+    assert L.or_scol(w, 1.0, 1.0) == pytest.approx(1.849, rel=0.01)
+    assert L.or_scol(w, 10.0, 10.0) == pytest.approx(1.968, rel=0.02)
+    assert L.or_scol(w, 10.0, 10.0) < L.or_scol(WATER, 10.0, 10.0) * 0.92
