@@ -130,7 +130,7 @@ def profiled_traffic(kernel: str, workload: str, key: str = "traffic_bytes_per_h
     tb = re.search(key + r": ([0-9.]+)", text)
     if not fp or not tb:
         return None
-    return float(tb.group(1)) if kernel_fingerprint() == fp.group(1) else None
+    return float(tb.group(1)) if kernel_fingerprint(kernel) == fp.group(1) else None
 
 
 def time_to_target(d, pid, wl, chunk, kernel, target=0.01, max_chunks=200):
@@ -182,16 +182,18 @@ def deposit_stream(raw, n, seed=0):
     return np.minimum(np.searchsorted(cdf, u, side="right"), len(w) - 1).astype(np.uint32)
 
 
-def kernel_fingerprint():
-    """First 16 hex digits of the sha256 of the transport kernel's sources
-    (dpm_device.cuh, dpm_queue.cu, dpm_internal.h) with comments and
+def kernel_fingerprint(kernel: str = "k_queue"):
+    """First 16 hex digits of the sha256 of a transport kernel's sources
+    (dpm_device.cuh and dpm_internal.h, with dpm_queue.cu for k_queue or
+    dpm_history.cu for the one-history-per-thread kernels) with comments and
     whitespace removed: edits to comments keep a capture valid."""
     import hashlib
     import re
 
     src = os.path.join(ROOT, "paper_0910_0329_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("dpm_device.cuh", "dpm_queue.cu", "dpm_internal.h"):
+    own = "dpm_queue.cu" if kernel == "k_queue" else "dpm_history.cu"
+    for f in ("dpm_device.cuh", own, "dpm_internal.h"):
         with open(os.path.join(src, f)) as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)

@@ -78,7 +78,10 @@ __device__ void reduce_counters(const long long *cnt, int err, const RunParams &
 
 constexpr int kHistStack = 64;
 
-__global__ void __launch_bounds__(128) k_history(const __grid_constant__ RunParams R, uint64_t batch_size) {
+// 8 resident blocks of 128 threads cap the registers at 64, as in the queue
+// kernel: the extra spills cost less than the doubled occupancy gains
+// (+26 % on 6 MV, +30 % on 20 MeV electrons against 128 registers).
+__global__ void __launch_bounds__(128, 8) k_history(const __grid_constant__ RunParams R, uint64_t batch_size) {
   Part stack[kHistStack];
   HistSink s(R, stack, kHistStack);
   const size_t V = size_t(R.P.nx) * R.P.ny * R.P.nz;

@@ -60,16 +60,25 @@ def grid(params=P):
     return np.exp(np.linspace(np.log(e_lo), np.log(e_hi), int(params["n_e"])))
 
 
+# The device finds a table position with the hardware logarithm: within
+# 7.2e-7 of ln E on the tables' range (3 ulp of |ln E| < 4, or 2^-21.41 on
+# [0.5, 2], the intrinsic's documented bounds), i.e. at most this many node
+# spacings off at the default grid.
+POS_ERR = 7.2e-7 * (P["n_e"] - 1) / math.log(1.01 * P["e_max"] / (0.99 * min(P["eabs_e"], P["eabs_g"])))
+
+
 def interp_tolerance(f, E, params=P):
     """Bound on linear interpolation in ln E of the oracle function f at E: a
     quarter of the largest second difference of f over the two node intervals
-    around E (h^2/8 f'' for smooth f, h/4 times the slope jump at a kink), plus
-    FP32 storage rounding."""
+    around E (h^2/8 f'' for smooth f, h/4 times the slope jump at a kink),
+    the position error of the device's logarithm times the largest first
+    difference, plus FP32 storage rounding."""
     g = grid(params)
     i = np.clip(np.searchsorted(g, E) - 1, 1, len(g) - 3)
     f0, f1, f2, f3 = (np.array([f(g[j]) for j in i + k]) for k in (-1, 0, 1, 2))
     d2 = np.maximum(np.abs(f2 - 2 * f1 + f0), np.abs(f3 - 2 * f2 + f1))
-    return d2 / 4.0 + 4e-7 * np.maximum(np.abs(f1), np.abs(f2))
+    d1 = np.maximum(np.maximum(np.abs(f1 - f0), np.abs(f2 - f1)), np.abs(f3 - f2))
+    return d2 / 4.0 + POS_ERR * d1 + 4e-7 * np.maximum(np.abs(f1), np.abs(f2))
 
 
 def check(got, f, E):
