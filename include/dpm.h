@@ -339,7 +339,8 @@ int dpm_diag_table(dpm_ctx *ctx, int which, int mat, int n, const double *energy
    4 MSC 1-mu for q = aux (mean of 1-mu), 5 6 MV spectrum energy,
    6 exponential path -ln(u) in mean free paths, 7 direction rotation: the
    unit vector (0.36, -0.48, 0.8) (aux 0..2) or +z (aux 3..5) turned by polar
-   cosine e and azimuth 2 pi u, its component int(aux) % 3. */
+   cosine e and azimuth 2 pi u, its component int(aux) % 3, 8 path from
+   x = u cm to the far face of a 1 cm voxel [0, 1) along direction cosine e. */
 int dpm_diag_sample(dpm_ctx *ctx, int which, double e, double aux, int n, const double *u, double *out);
 
 /* n Philox4x32-10 blocks for counters ctr[4*i..] and keys key[2*i..] (host). */

@@ -680,7 +680,7 @@ int dpm_diag_table(dpm_ctx *c, int which, int mat, int n, const double *energy, 
 int dpm_diag_sample(dpm_ctx *c, int which, double e, double aux, int n, const double *u, double *out) {
   if (!c) return DPM_EINVAL;
   if (!c->tables_ready) return fail(c, DPM_ESTATE, "no tables");
-  if (n < 0 || (n > 0 && (!u || !out)) || which < 0 || which > 7) return fail(c, DPM_EINVAL, "bad arguments");
+  if (n < 0 || (n > 0 && (!u || !out)) || which < 0 || which > 8) return fail(c, DPM_EINVAL, "bad arguments");
   if (n == 0) return DPM_OK;
   cudaSetDevice(c->device);
   double *d = nullptr;

@@ -123,9 +123,12 @@ __device__ __forceinline__ Part child(const Part &p, int type, uint32_t ordinal)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int vox(const Part &p, const DevPhantom &P) { return p.ix + P.nx * (p.iy + P.ny * p.iz); }
 
+// Path length to the next face along one axis.  The hardware division (2 ulp)
+// suffices: a step that reaches a face puts the coordinate on the face
+// exactly (cross_face), so its error only moves the step length by 2 ulp.
 __device__ __forceinline__ float face_dist(float x, float u, int i, float d) {
-  if (u > 0.f) return fmaxf((float(i + 1) * d - x) / u, 0.f);
-  if (u < 0.f) return fmaxf((float(i) * d - x) / u, 0.f);
+  if (u > 0.f) return fmaxf(__fdividef(float(i + 1) * d - x, u), 0.f);
+  if (u < 0.f) return fmaxf(__fdividef(float(i) * d - x, u), 0.f);
   return kInf;
 }
 
@@ -256,7 +259,7 @@ __device__ __forceinline__ float samp(const SampTab &t, float lnE, float u) {
 // A of the random-hinge distribution for a step of x = s/lambda1: the table is
 // ln A against logit(q), q = 1 - exp(-x); beyond its ends ln A grows like logit(q).
 __device__ __forceinline__ float msc_A(const DevTables &T, float x) {
-  const float lg = logf(-expm1f(-x)) + x;
+  const float lg = __logf(-expm1f(-x)) + x;  // hardware logarithm: the table position moves by ~1e-6
   const float t = (lg - T.msc_x0) * T.msc_inv_dx;
   float lA;
   if (!(t > 0.f)) {  // also catches NaN

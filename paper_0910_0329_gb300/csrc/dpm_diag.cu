@@ -84,6 +84,12 @@ __global__ void k_diag_sample(DevTables T, int which, float e, float aux, int n,
       r = (a % 3 == 0) ? du : (a % 3 == 1) ? dv : dw;
       break;
     }
+    case 8: {
+      // path from x (cm) inside voxel 0 of 1 cm voxels to its face along a
+      // direction of cosine e to the axis
+      r = face_dist(x, e, 0, 1.f);
+      break;
+    }
     default: r = 0.0;
   }
   out[i] = r;

@@ -117,3 +117,19 @@ def test_rotation(tables_ctx, c):
         assert np.max(np.abs(gram - s2 * np.cos(phi[:, None] - phi[None, :]))) < 8e-6
         # increasing azimuth turns right-handed about the old direction
         assert np.dot(np.cross(perp[0], perp[16]), d) == pytest.approx(s2 * np.sin(phi[16] - phi[0]), abs=8e-6)
+
+
+def test_face_distance(tables_ctx):
+    """The path to a voxel face with the hardware division: within 2 ulp of the
+    quotient (the intrinsic's documented bound, 4 * 2^-24 relative) plus half
+    an ulp for the numerator's rounding, against FP64 on the device's float
+    inputs."""
+    x = np.linspace(0.0, 0.999, 500)
+    xf = x.astype(np.float32).astype(np.float64)
+    for c in (1.0, 0.7, 0.05, 1e-4, -0.3):
+        got = dpm.dpm_diag_sample(tables_ctx.ctx, 8, c, 0.0, x)
+        cf = float(np.float32(c))
+        ref = (1.0 - xf) / cf if cf > 0 else (0.0 - xf) / cf
+        ref = np.maximum(ref, 0.0)
+        assert np.all(got >= 0.0)
+        assert np.all(np.abs(got - ref) <= 6 * 2.0 ** -24 * ref + 1e-30), (c, np.max(np.abs(got - ref) / np.maximum(ref, 1e-30)))
