@@ -185,7 +185,7 @@ __device__ __forceinline__ void rotate(float &u, float &v, float &w, float c, fl
     nv = s * sp;
     nw = (w >= 0.f) ? c : -c;
   } else {
-    const float r = sqrtf(r2), a = s / r;
+    const float ir = rsqrtf(r2), r = r2 * ir, a = s * ir;  // hardware 1/sqrt; renormalised below
     nu = u * c + a * (u * w * cp - v * sp);
     nv = v * c + a * (v * w * cp + u * sp);
     nw = w * c - s * r * cp;
@@ -273,8 +273,9 @@ __device__ __forceinline__ float msc_A(const DevTables &T, float x) {
   return __expf(fminf(lA, 60.f));  // hardware exponential: a few ulp at the ln A of real steps
 }
 
-// 1 - mu of the hinge distribution by its inverse CDF.
-__device__ __forceinline__ float msc_sample(float A, float xi) { return 2.f * A * xi / (1.f + A - xi); }
+// 1 - mu of the hinge distribution by its inverse CDF (hardware division,
+// 2 ulp: far below the table's interpolation error).
+__device__ __forceinline__ float msc_sample(float A, float xi) { return __fdividef(2.f * A * xi, 1.f + A - xi); }
 
 // Kinetic energy after a CSDA mass path mp from T0 (range R0, stopping power S0
 // at T0): Euler estimate refined by one Newton step on the range table.  For
@@ -563,9 +564,9 @@ __device__ bool electron_step(Part &p, const Ctx &R, Sink &s) {
   const float Tend = fmaxf((1.f - T.f_e) * T0, T.eabs_e);
   const float4 r0 = el_at(T, m, eidx_x(T, x0));  // R, S, Sigma_hard, 1/lambda1
   const float Rend = el_at(T, m, eidx_x(T, xe)).x;
-  const float sE = fmaxf(r0.x - Rend, 0.f) / rho;
+  const float sE = __fdividef(fmaxf(r0.x - Rend, 0.f), rho);  // path lengths: hardware division (2 ulp)
   const uint4 rn = draw(p, R);
-  const float sh = (r0.z > 0.f && !(T.flags & DPM_NO_HARD)) ? neglog(u01(rn.x)) / (rho * r0.z) : kInf;
+  const float sh = (r0.z > 0.f && !(T.flags & DPM_NO_HARD)) ? __fdividef(neglog(u01(rn.x)), rho * r0.z) : kInf;
   const bool hard = sh < sE;
   const float st = hard ? sh : sE;
   const float tau = u01(rn.y);
