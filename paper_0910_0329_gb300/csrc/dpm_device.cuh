@@ -174,7 +174,8 @@ __device__ __forceinline__ void locate(Part &p, const DevPhantom &P) {
 // accurate to about 2^-21 absolute; the direction is renormalised below.
 __device__ __forceinline__ void rotate(float &u, float &v, float &w, float c, float h) {
   c = fminf(fmaxf(c, -1.f), 1.f);
-  const float s = sqrtf(fmaxf(0.f, 1.f - c * c));
+  const float c2 = fmaxf(0.f, 1.f - c * c);
+  const float s = c2 * rsqrtf(fmaxf(c2, 1e-30f));  // sin(theta) by the hardware 1/sqrt
   float sp, cp;
   const float t = h - 2.f * floorf(0.5f * h + 0.5f);  // h modulo 2, in [-1, 1)
   __sincosf(3.14159265f * t, &sp, &cp);
@@ -259,7 +260,12 @@ __device__ __forceinline__ float samp(const SampTab &t, float lnE, float u) {
 // A of the random-hinge distribution for a step of x = s/lambda1: the table is
 // ln A against logit(q), q = 1 - exp(-x); beyond its ends ln A grows like logit(q).
 __device__ __forceinline__ float msc_A(const DevTables &T, float x) {
-  const float lg = __logf(-expm1f(-x)) + x;  // hardware logarithm: the table position moves by ~1e-6
+  // q = 1 - exp(-x): a Taylor polynomial below x = 0.1 (truncation under
+  // 1e-7 relative), the hardware exponential above (2 ulp of exp(-x), at
+  // most 3e-6 of q); the hardware logarithm then moves the table position
+  // by a few 1e-6
+  const float q = x < 0.1f ? x * (1.f - x * (0.5f - x * (1.f / 6.f - x * (1.f / 24.f)))) : 1.f - __expf(-x);
+  const float lg = __logf(q) + x;
   const float t = (lg - T.msc_x0) * T.msc_inv_dx;
   float lA;
   if (!(t > 0.f)) {  // also catches NaN
