@@ -18,7 +18,6 @@ enters through the plane ``z = 0``.
 """
 from __future__ import annotations
 
-import math
 from dataclasses import dataclass, field
 
 import numpy as np
