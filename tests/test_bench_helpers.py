@@ -60,3 +60,32 @@ def test_kernel_table_matches_the_binding():
 
 def test_max_over_ranks_on_one_rank():
     assert bench.max_over_ranks(3.5, 1, 0) == 3.5
+
+
+class _FakeSmi:
+    """Stands in for the nvidia-smi process: its sampled CSV lines."""
+
+    def __init__(self, text):
+        self.text = text
+
+    def terminate(self):
+        pass
+
+    def communicate(self, timeout=None):
+        return self.text, ""
+
+
+def test_clock_samples_are_summarised():
+    c = bench.Clocks(0)
+    c.proc = _FakeSmi("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                      "0, 2055, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+                      "0, 2070, 2070, 1201.5, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                      "garbage line\n"
+                      "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    r = c.stop()
+    assert r == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c = bench.Clocks(0)
+    c.proc = _FakeSmi("0, 1500, 2070, 700, 0x8, Active, Not Active, Active, Not Active\n")
+    assert c.stop()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    c = bench.Clocks(0)  # never started: no nvidia-smi
+    assert c.stop()["samples"] == 0
