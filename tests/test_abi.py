@@ -84,3 +84,40 @@ def test_struct_fields_match_the_c_compiler(tmp_path):
                     str(exe)], check=True, capture_output=True)
     got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got == expect
+
+
+def test_every_entry_point_rejects_a_null_handle_without_a_gpu():
+    """The header's error contract for a null context or server: DPM_EINVAL
+    from every call that takes one, before any CUDA call (so this runs on a
+    machine without a GPU); destroy calls are no-ops and the last error of a
+    null context is a fixed message."""
+    L = ctypes.CDLL(build_lib.build())
+    skip = {"dpm_host_tables_build", "dpm_host_tables_get", "dpm_host_tables_free", "dpm_serve_next_chunk",
+            "dpm_serve_select", "dpm_last_error", "dpm_destroy", "dpm_server_destroy"}
+    checked = 0
+    for name, (res, args) in sorted(dpm._SIGS.items()):
+        if name in skip:
+            continue
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+        vals = []
+        for a in args:
+            if a in (ctypes.c_double, ctypes.c_float):
+                vals.append(0.0)
+            elif a in (ctypes.c_int, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64,
+                       ctypes.c_size_t):
+                vals.append(0)
+            else:
+                vals.append(None)
+        assert f(*vals) == dpm.DPM_EINVAL, name
+        checked += 1
+    assert checked == len([n for n in dpm._SIGS if n not in skip]) and checked > 20
+    for name in ("dpm_destroy", "dpm_server_destroy"):
+        f = getattr(L, name)
+        f.restype, f.argtypes = None, [ctypes.c_void_p]
+        f(None)
+    f = L.dpm_last_error
+    f.restype, f.argtypes = ctypes.c_char_p, [ctypes.c_void_p]
+    assert f(None) == b"null context"
+    # the pure policies: no options size nothing, an empty queue selects nothing
+    assert L.dpm_serve_next_chunk(None, ctypes.c_uint64(10), ctypes.c_double(0.1)) == 0
