@@ -290,7 +290,10 @@ void dpm_server_destroy(dpm_server *server);
    DPM_EINVAL for a bad geometry id or a null pointer. */
 int dpm_server_submit(dpm_server *server, int geometry_id, const dpm_source *src, uint64_t seed, int *request_id);
 /* One round (synchronous); *n_completed receives the requests it finished.
-   Does nothing when no request is active or admissible. */
+   Does nothing when no request is active or admissible.  If it returns an
+   error the round's requests keep their state from before the round, but
+   their tallies may hold part of the failed round: release them only after
+   reading, and resubmit. */
 int dpm_server_round(dpm_server *server, int *n_completed);
 /* A request's state and statistics; DPM_EINVAL for a bad id. */
 int dpm_server_status(dpm_server *server, int request_id, dpm_request_status *status);
