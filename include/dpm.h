@@ -292,8 +292,9 @@ int dpm_server_submit(dpm_server *server, int geometry_id, const dpm_source *src
 /* One round (synchronous); *n_completed receives the requests it finished.
    Does nothing when no request is active or admissible.  If it returns an
    error the round's requests keep their state from before the round, but
-   their tallies may hold part of the failed round: release them only after
-   reading, and resubmit. */
+   their tallies may hold part of the failed round: destroy the server and
+   resubmit the requests to a new one (the old slots stay phantoms of the
+   context until dpm_free_phantom or dpm_destroy). */
 int dpm_server_round(dpm_server *server, int *n_completed);
 /* A request's state and statistics; DPM_EINVAL for a bad id. */
 int dpm_server_status(dpm_server *server, int request_id, dpm_request_status *status);
