@@ -150,3 +150,21 @@ def test_field_projection_on_surface():
     inside = np.abs(xc) < 4.5 + 0.5
     assert d0[:, ~inside].sum() == 0.0
     assert d0[np.ix_(np.abs(xc) < 4.0, np.abs(xc) < 4.0)].min() > 0
+
+
+MATERIALS_DE = [dict(W.WATER, rho_de=1.0), dict(W.LUNG, rho_de=0.3), dict(W.BONE, rho_de=1.85)]
+
+
+def test_density_effect_transport_conserves_energy_and_lengthens_ranges():
+    """With the density-effect correction (R20) the transport still conserves
+    energy per history, and the lower stopping power lengthens the CSDA path
+    above X0 while leaving it unchanged below (delta = 0 under 0.445 MeV in
+    water)."""
+    wl = W.c0_electron_wlw()
+    r = O.run(wl.phantom, MATERIALS_DE, wl.params, wl.source, 150, wl.seed, workers=2)
+    assert r.stats["max_balance_rel"] < 1e-9
+    L = O.lib()
+    pr = O.params(P)
+    w, w0 = O.material(MATERIALS_DE[0]), O.material(W.WATER)
+    assert L.or_csda_path(w, pr, 0.2, 0.44) == pytest.approx(L.or_csda_path(w0, pr, 0.2, 0.44), rel=1e-12)
+    assert L.or_csda_path(w, pr, 0.2, 20.0) > 1.05 * L.or_csda_path(w0, pr, 0.2, 20.0)
