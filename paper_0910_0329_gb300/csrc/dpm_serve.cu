@@ -86,7 +86,8 @@ size_t slot_bytes(dpm_server *s, PhantomState *p) {
 
 Geometry &sized_geometry(dpm_server *s, int g) {
   Geometry &G = geometry(s, g);
-  if (!G.slot_bytes) G.slot_bytes = slot_bytes(s, ctx_phantom(s->ctx, g));
+  PhantomState *p = ctx_phantom(s->ctx, g);
+  if (!G.slot_bytes && p) G.slot_bytes = slot_bytes(s, p);
   return G;
 }
 
@@ -95,6 +96,10 @@ Geometry &sized_geometry(dpm_server *s, int g) {
 // -1 if none (the request waits).
 int take_slot(dpm_server *s, int g, int &rc) {
   rc = DPM_OK;
+  if (!ctx_phantom(s->ctx, g)) {  // the geometry was freed after the request was submitted
+    rc = srv_fail(s, DPM_EINVAL, "a request's geometry is no longer loaded");
+    return -1;
+  }
   Geometry &G = sized_geometry(s, g);
   if (!G.free_slots.empty()) {
     const int id = G.free_slots.back();
