@@ -412,7 +412,7 @@ def main():
     line["time_to_1pct_sigma_at_dmax_measured"] = time_to_target(d, pid, wl, n, kernel)
 
     if not args.no_e2e:
-        line["e2e"] = e2e(args, d, wl, n, kernel, local)
+        line["e2e"] = e2e(args, d, wl, n, kernel, local, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, wl)
     d.close()
@@ -609,10 +609,11 @@ def bench_paper_table1(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
-def e2e(args, d, wl, n, kernel, local):
+def e2e(args, d, wl, n, kernel, local, rank=0, world=1):
     """Same metric through the public C ABI with host buffers: every step
     copies the phantom from pinned host memory, transports, and reads dose and
-    sigma back into host memory."""
+    sigma back into host memory.  Under torchrun each rank runs its own
+    history ranges and the job's rate takes the slowest rank's step time."""
     import torch
 
     from paper_0910_0329_gb300 import dpm
@@ -635,7 +636,7 @@ def e2e(args, d, wl, n, kernel, local):
         rc = L.dpm_update_phantom(d.ctx, pid, mat.data_ptr(), rho.data_ptr())
         if rc:
             raise dpm.DpmError(rc, L.dpm_last_error(d.ctx).decode())
-        dpm.dpm_run(d.ctx, pid, wl.source, i * n, n, wl.seed, dpm.run_opts(kernel=kernel))
+        dpm.dpm_run(d.ctx, pid, wl.source, (i * world + rank) * n, n, wl.seed, dpm.run_opts(kernel=kernel))
         st = dpm.dpm_run_stats()
         rc = L.dpm_read_dose(d.ctx, pid, dose.data_ptr(), sig.data_ptr(), s1.data_ptr(), dpm.C.byref(st))
         if rc:
@@ -643,9 +644,9 @@ def e2e(args, d, wl, n, kernel, local):
         if i > 0:
             times.append(time.perf_counter() - t)
     dpm.dpm_free_phantom(d.ctx, pid)
-    t = statistics.mean(times)
-    return {"value": n / t, "unit": "histories/s", "h2d_bytes_per_step": ph.n_vox * 5,
-            "d2h_bytes_per_step": ph.n_vox * (8 + 8 + 8) + 8 * 8 + 4,
+    t = max_over_ranks(statistics.mean(times), world, local)
+    return {"value": world * n / t, "unit": "histories/s", "h2d_bytes_per_step": world * ph.n_vox * 5,
+            "d2h_bytes_per_step": world * (ph.n_vox * (8 + 8 + 8) + 8 * 8 + 4),
             "what": "dpm_update_phantom (pinned host mat+rho) + dpm_run + dpm_read_dose (host dose, sigma, raw)"}
 
 
