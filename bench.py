@@ -646,7 +646,7 @@ def e2e(args, d, wl, n, kernel, local, rank=0, world=1):
     dpm.dpm_free_phantom(d.ctx, pid)
     t = max_over_ranks(statistics.mean(times), world, local)
     return {"value": world * n / t, "unit": "histories/s", "h2d_bytes_per_step": world * ph.n_vox * 5,
-            "d2h_bytes_per_step": world * (ph.n_vox * (8 + 8 + 8) + 8 * 8 + 4),
+            "d2h_bytes_per_step": world * (ph.n_vox * (8 + 8 + 8) + dpm.C.sizeof(dpm.dpm_run_stats)),
             "what": "dpm_update_phantom (pinned host mat+rho) + dpm_run + dpm_read_dose (host dose, sigma, raw)"}
 
 
