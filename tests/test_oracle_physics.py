@@ -187,21 +187,54 @@ def test_hard_cross_sections_increase_with_energy(L):
         assert (np.diff(s) >= 0).all()
 
 
-def test_lambda1_bracket_is_transport_integral(L):
-    # the bracket ln(1+1/eta) - 1/(1+eta) is the integral of (1-mu)/(1-mu+2eta)^2 dmu;
-    # check that lambda1^-1 equals 2 pi n Z(Z+1) re^2/(beta^4 gamma^2) times that integral
-    T = 2.0
-    t = T / MC2
-    g = t + 1
-    b2 = 1 - 1 / g ** 2
-    bg2 = t * (t + 2)
-    alpha = 1 / 137.035999084
-    tot = 0.0
-    for Z, A, w in W.WATER["elements"]:
-        eta = 0.25 * (alpha * Z ** (1 / 3) / 0.885) ** 2 / bg2 * (1.13 + 3.76 * (alpha * Z) ** 2 / b2)
-        integ = quad(lambda mu: (1 - mu) / (1 - mu + 2 * eta) ** 2, -1, 1, points=[1 - 1e-3, 1 - 1e-5])
-        tot += NA * w / A * 2 * math.pi * Z * (Z + 1) * RE ** 2 / (b2 * bg2) * integ
-    assert L.or_lambda1_inv(WATER, T) == pytest.approx(tot, rel=1e-8)
+# CODATA 2018 values used only by the screening pin below: the reduced Planck
+# constant times c and the Bohr radius, so that the screening angle is built
+# from hbar / (p a_TF) and not from the fine-structure constant
+HBARC_MEV_CM = 197.3269804e-13
+BOHR_CM = 0.529177210903e-8
+
+
+def _screened_rutherford_transport(Z, T):
+    """Transport cross section per atom (cm^2) of the screened Rutherford
+    (Wentzel) elastic model, from its physical definition (Sec. 2.1's condensed
+    elastic scattering): Moliere's screening angle chi0 = hbar/(p a_TF) with the
+    Thomas-Fermi radius a_TF = 0.885 a0 Z^-1/3 and his Coulomb correction
+    (1.13 + 3.76 (alpha Z/beta)^2), screening parameter eta = chi0^2/4, and the
+    Rutherford prefactor (Z e^2/(p v))^2 with nuclear plus atomic-electron
+    scattering Z(Z+1); integrated numerically over the polar angle theta."""
+    pc = math.sqrt(T * (T + 2 * MC2))  # MeV
+    beta = pc / (T + MC2)
+    a_tf = 0.885 * BOHR_CM * Z ** (-1.0 / 3.0)
+    chi0_sq = (HBARC_MEV_CM / (pc * a_tf)) ** 2 * (1.13 + 3.76 * (Z / 137.035999084 / beta) ** 2)
+    eta = chi0_sq / 4.0
+    # e^2/(p v) = r_e mc^2 / (pc beta)
+    pref = Z * (Z + 1) * (RE * MC2 / (pc * beta)) ** 2
+    f = lambda th: (1 - math.cos(th)) * pref / (1 - math.cos(th) + 2 * eta) ** 2 * 2 * math.pi * math.sin(th)
+    th0 = 2 * math.sqrt(eta)  # the screening angle: the integrand peaks near it
+    return quad(f, 0.0, math.pi, points=[th0 / 10, th0, 10 * th0, 100 * th0]), eta
+
+
+@pytest.mark.parametrize("Z,A", [(1.0, 1.008), (8.0, 15.999), (13.8, 13.8 / 0.5148)])
+@pytest.mark.parametrize("T", [0.3, 2.0, 20.0])
+def test_lambda1_from_screening_angle(L, Z, A, T):
+    # the oracle's 1/lambda1 of a one-element material against the transport
+    # cross section built from hbar, a0 and p (not from alpha) and integrated
+    # over theta: a lost 1/4, 0.885 inverted, beta written for beta*gamma or a
+    # wrong 3.76 term each move eta by a large factor and 1/lambda1 by >1e-3
+    m = O.material({"elements": [(Z, A, 1.0)], "i_ev": 75.0})
+    sig_tr, eta = _screened_rutherford_transport(Z, T)
+    assert 1e-9 < eta < 1e-2
+    assert L.or_lambda1_inv(m, T) == pytest.approx(NA / A * sig_tr, rel=1e-9)
+
+
+def test_lambda1_screening_sensitivity():
+    # the pin above resolves the plausible slips: each changes 1/lambda1 by
+    # far more than its 1e-9 tolerance
+    Z, T = 8.0, 2.0
+    base, eta = _screened_rutherford_transport(Z, T)
+    br = lambda e: math.log1p(1 / e) - 1 / (1 + e)
+    for wrong in [4 * eta, eta / 0.885 ** 4, eta * (T + MC2) ** 2 / MC2 ** 2]:
+        assert abs(br(wrong) / br(eta) - 1) > 1e-3
 
 
 def test_csda_path_vs_scipy(L):
