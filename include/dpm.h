@@ -47,7 +47,9 @@ typedef enum {
     DPM_ECUDA = -3,           /* a CUDA runtime call failed (message has the CUDA error) */
     DPM_EQUEUE_OVERFLOW = -4, /* a particle queue or stack overflowed: rerun with larger capacity */
     DPM_ETIMEOUT = -5,        /* a bounded device wait gave up */
-    DPM_ESTATE = -6           /* call out of order (e.g. run before tables) */
+    DPM_ESTATE = -6,          /* call out of order (e.g. run before tables) */
+    DPM_ESTEPCAP = -7         /* a particle exceeded its step or flight limit (far above any
+                                 real track); its remaining energy was deposited where it stopped */
 } dpm_status;
 
 #define DPM_MAX_ELEM 8
@@ -139,9 +141,20 @@ typedef struct {
                                      the secondary phase (0 for the per-history kernel) */
 } dpm_run_stats;
 
-int dpm_create(dpm_ctx **out, int cuda_device);
+/* A context on CUDA device `cuda_device`.  hbm_budget_bytes (0 = no limit)
+   bounds the device memory the context keeps: tables, phantoms, tallies,
+   particle queues, batch and server buffers, and the diagnostics' temporary
+   buffers while they live.  An allocation that would exceed it fails with
+   DPM_ENOMEM before calling cudaMalloc, and the call that needed it fails
+   with that status (a run's admission control; the request server applies
+   its own budget to its slots on top).  DPM_ECUDA if the device is absent.
+   The call also loads, on that device, the library's kernels and the fixed
+   scratch of dpm_run_noalloc() (see there). */
+int dpm_create(dpm_ctx **out, int cuda_device, uint64_t hbm_budget_bytes);
 void dpm_destroy(dpm_ctx *ctx);
 const char *dpm_last_error(const dpm_ctx *ctx);
+/* Device bytes the context holds now and its budget (either may be NULL). */
+int dpm_device_bytes(const dpm_ctx *ctx, uint64_t *in_use, uint64_t *budget);
 
 /* Use an external CUDA stream (cudaStream_t passed as void*); NULL restores
    the context's own stream.  Waits for the work queued on the previous stream
@@ -379,20 +392,34 @@ int dpm_diag_atomic_replay(dpm_ctx *ctx, const uint32_t *ids, uint64_t n, uint64
    physics and random numbers for histories [first_history, first_history +
    n_histories) and ADDS the integer tally (units of 2^-32 MeV, nx*ny*nz
    int64, voxel layout as above) to the caller-allocated device array d_tally;
-   no batch statistics are kept.  Its scratch (particle queues, counters, error
-   word) is a fixed device array of DPM_NOALLOC_SCRATCH_BYTES that every GPU
-   loading the library holds until the process exits; the call allocates
-   nothing.  The first call on a device looks the array's device address up
-   (cudaGetSymbolAddress), so that first call should come before any stream
-   capture.  Every call shares the one array: calls that overlap on the GPU
-   (e.g. from two contexts or streams at once) race and must be serialised by
-   the caller.  The call waits for the transport and returns its status:
-   DPM_EQUEUE_OVERFLOW if the fixed queues overflowed, DPM_ETIMEOUT if a bounded
-   wait gave up, DPM_ESTATE before dpm_build_tables(), DPM_EINVAL for bad
-   arguments or more than 2^31-1 histories. */
+   no batch statistics are kept.
+   Memory: its scratch (particle queues, counters, error word) is a fixed
+   device array of DPM_NOALLOC_SCRATCH_BYTES.  The driver places that array in
+   a device's memory when it loads the library's module holding it there;
+   dpm_create() forces that load (and the load of the queue kernels) on its
+   device, so that after dpm_create() this call allocates nothing, and the
+   array then stays on the device until the process exits.  The call looks
+   the array's device address up each time (cudaGetSymbolAddress, no
+   allocation once loaded); it never calls cudaMalloc, cudaFree or an
+   allocating library routine.
+   Sharing: every call in the process shares the one array, which keeps the
+   last call's contents (each call clears the counters it uses): calls that
+   overlap on the GPU (e.g. from two contexts or streams at once) race and must
+   be serialised by the caller.
+   Result: the call waits for the transport and returns its status.  On
+   success d_tally holds its previous contents plus this run's tally.  On
+   DPM_EQUEUE_OVERFLOW (the fixed queues overflowed), DPM_ETIMEOUT (a bounded
+   wait gave up) or DPM_ESTEPCAP (a particle hit the step limit), part of the
+   run has already been added to d_tally and the amount is unknown: discard
+   d_tally or restore it from a copy.  DPM_ESTATE before dpm_build_tables(),
+   DPM_EINVAL for bad arguments or more than 2^31-1 histories (d_tally
+   untouched).  stats (host, may be NULL) receives the run's counters
+   (emitted, escaped and missed energy, steps, flights, atomics, pushes, error
+   flags) with `deposited` set to NaN: the deposited energy is the increase of
+   the caller's d_tally times 2^-32 MeV. */
 #define DPM_NOALLOC_SCRATCH_BYTES (48u << 20)
 int dpm_run_noalloc(dpm_ctx *ctx, int phantom_id, const dpm_source *src, uint64_t first_history,
-                    uint64_t n_histories, uint64_t seed, int64_t *d_tally);
+                    uint64_t n_histories, uint64_t seed, int64_t *d_tally, dpm_run_stats *stats);
 
 #ifdef __cplusplus
 }

@@ -58,38 +58,49 @@ int fail(dpm_ctx *c, int code, const std::string &msg) {
     if (e_ != cudaSuccess) return fail(ctx, DPM_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
   } while (0)
 
+// Device allocation owned by the context, counted against its budget.
 template <class T>
 int dalloc(dpm_ctx *c, T **p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 1;
-  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+  const size_t bytes = n * sizeof(T);
+  if (c->budget && c->in_use + bytes > c->budget)
+    return fail(c, DPM_ENOMEM, "device-memory budget of the context exceeded (" + std::to_string(c->in_use) +
+                                   " bytes in use, " + std::to_string(bytes) + " more asked, budget " +
+                                   std::to_string(c->budget) + ")");
+  cudaError_t e = cudaMalloc((void **)p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
     return fail(c, DPM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   }
+  c->alloc_bytes[*p] = bytes;
+  c->in_use += bytes;
   return DPM_OK;
 }
 
-void free_phantom(PhantomState *p) {
+// Free a context allocation made by dalloc (NULL is ignored).
+void dfree(dpm_ctx *c, void *p) {
+  if (!p) return;
+  auto it = c->alloc_bytes.find(p);
+  if (it != c->alloc_bytes.end()) {
+    c->in_use -= it->second;
+    c->alloc_bytes.erase(it);
+  }
+  cudaFree(p);
+}
+
+void free_phantom(dpm_ctx *c, PhantomState *p) {
   if (!p) return;
   drop_events(p);
-  cudaFree(p->d_mat);
-  cudaFree(p->d_rho);
-  cudaFree(p->d_mumax);
-  cudaFree(p->d_slabs);
-  cudaFree(p->d_fslabs);
-  cudaFree(p->d_S1);
-  cudaFree(p->d_Q);
-  cudaFree(p->d_counters);
-  cudaFree(p->d_inv_nb);
-  cudaFree(p->d_dose);
-  cudaFree(p->d_sigma);
-  cudaFree(p->d_dmax);
+  for (void *d : {(void *)p->d_mat, (void *)p->d_rho, (void *)p->d_mumax, (void *)p->d_slabs, (void *)p->d_fslabs,
+                  (void *)p->d_S1, (void *)p->d_Q, (void *)p->d_counters, (void *)p->d_inv_nb, (void *)p->d_dose,
+                  (void *)p->d_sigma, (void *)p->d_dmax})
+    dfree(c, d);
 }
 
 void free_tables(dpm_ctx *c) {
-  for (void *p : c->table_mem) cudaFree(p);
+  for (void *p : c->table_mem) dfree(c, p);
   c->table_mem.clear();
   c->tables_ready = false;
 }
@@ -150,7 +161,7 @@ int ctx_prepare_batches(dpm_ctx *c, PhantomState *p, uint64_t n, int n_batches, 
   B = int((n + bs - 1) / bs);
   int rc;
   if (p->slab_batches < size_t(B)) {
-    cudaFree(p->d_slabs);
+    dfree(c, p->d_slabs);
     p->d_slabs = nullptr;
     p->slab_batches = 0;
     if ((rc = dalloc(c, &p->d_slabs, size_t(B) * p->V))) return rc;
@@ -216,7 +227,7 @@ int ctx_run_params(dpm_ctx *c, PhantomState *p, const dpm_source *src, uint64_t 
 
 extern "C" {
 
-int dpm_create(dpm_ctx **out, int cuda_device) {
+int dpm_create(dpm_ctx **out, int cuda_device, uint64_t hbm_budget_bytes) {
   if (!out) return DPM_EINVAL;
   *out = nullptr;
   int n = 0;
@@ -227,6 +238,9 @@ int dpm_create(dpm_ctx **out, int cuda_device) {
   dpm_ctx *c = new (std::nothrow) dpm_ctx();
   if (!c) return DPM_ENOMEM;
   c->device = cuda_device;
+  c->budget = hbm_budget_bytes;
+  c->queue.budget = hbm_budget_bytes;
+  c->queue.in_use = &c->in_use;
   if (cudaSetDevice(cuda_device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, cuda_device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
@@ -236,6 +250,13 @@ int dpm_create(dpm_ctx **out, int cuda_device) {
     return DPM_ECUDA;
   }
   c->stream = c->own;
+  // load the no-allocation entry point's scratch and the queue kernels now,
+  // so that dpm_run_noalloc() finds them resident
+  std::string err;
+  if (noalloc_setup(err) != DPM_OK) {
+    dpm_destroy(c);
+    return DPM_ECUDA;
+  }
   *out = c;
   return DPM_OK;
 }
@@ -244,12 +265,12 @@ void dpm_destroy(dpm_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
-  for (auto &p : c->phantoms) free_phantom(p.get());
+  for (auto &p : c->phantoms) free_phantom(c, p.get());
   free_tables(c);
   queue_free(c->queue);
-  cudaFree(c->d_jobs);
-  cudaFree(c->d_dmax_out);
-  cudaFree(c->d_batch_counters);
+  dfree(c, c->d_jobs);
+  dfree(c, c->d_dmax_out);
+  dfree(c, c->d_batch_counters);
   for (cudaEvent_t e : c->batch_ev) cudaEventDestroy(e);
   if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
   cudaFree(c->d_err);
@@ -258,6 +279,13 @@ void dpm_destroy(dpm_ctx *c) {
 }
 
 const char *dpm_last_error(const dpm_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int dpm_device_bytes(const dpm_ctx *c, uint64_t *in_use, uint64_t *budget) {
+  if (!c) return DPM_EINVAL;
+  if (in_use) *in_use = c->in_use;
+  if (budget) *budget = c->budget;
+  return DPM_OK;
+}
 
 int dpm_set_stream(dpm_ctx *c, void *s) {
   if (!c) return DPM_EINVAL;
@@ -301,7 +329,7 @@ int dpm_load_phantom(dpm_ctx *c, int nx, int ny, int nz, double dx, double dy, d
   if ((rc = dalloc(c, &p->d_mat, p->V)) || (rc = dalloc(c, &p->d_rho, p->V)) || (rc = dalloc(c, &p->d_S1, p->V)) ||
       (rc = dalloc(c, &p->d_Q, p->V)) || (rc = dalloc(c, &p->d_counters, size_t(kCounterSlots))) ||
       (rc = dalloc(c, &p->d_inv_nb, size_t(1024))) || (rc = dalloc(c, &p->d_mumax, size_t(kMaxTableNodes)))) {
-    free_phantom(p.get());
+    free_phantom(c, p.get());
     return rc;
   }
   CUDA_TRY(c, cudaMemcpyAsync(p->d_mat, mat, p->V, cudaMemcpyHostToDevice, c->stream));
@@ -311,7 +339,7 @@ int dpm_load_phantom(dpm_ctx *c, int nx, int ny, int nz, double dx, double dy, d
   CUDA_TRY(c, cudaMemsetAsync(p->d_counters, 0, kCounterSlots * sizeof(unsigned long long), c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if ((rc = update_mumax(c, p.get()))) {
-    free_phantom(p.get());
+    free_phantom(c, p.get());
     return rc;
   }
   p->uid = c->next_phantom_uid++;
@@ -326,7 +354,7 @@ int dpm_free_phantom(dpm_ctx *c, int id) {
   if (!p) return fail(c, DPM_EINVAL, "bad phantom id");
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
-  free_phantom(p);
+  free_phantom(c, p);
   c->phantoms[id].reset();
   return DPM_OK;
 }
@@ -398,7 +426,7 @@ int dpm_clone_phantom(dpm_ctx *c, int src_id, int *phantom_id) {
   if ((rc = dalloc(c, &p->d_mat, p->V)) || (rc = dalloc(c, &p->d_rho, p->V)) || (rc = dalloc(c, &p->d_S1, p->V)) ||
       (rc = dalloc(c, &p->d_Q, p->V)) || (rc = dalloc(c, &p->d_counters, size_t(kCounterSlots))) ||
       (rc = dalloc(c, &p->d_inv_nb, size_t(1024))) || (rc = dalloc(c, &p->d_mumax, size_t(kMaxTableNodes)))) {
-    free_phantom(p.get());
+    free_phantom(c, p.get());
     return rc;
   }
   // device-to-device, ordered on the context's stream after any pending work
@@ -470,7 +498,7 @@ int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t 
   int B = 0;
   if ((rc = ctx_prepare_batches(c, p, n, o.n_batches, bs, B))) return rc;
   if (paper && p->fslab_batches < size_t(B)) {
-    cudaFree(p->d_fslabs);
+    dfree(c, p->d_fslabs);
     p->d_fslabs = nullptr;
     p->fslab_batches = 0;
     if ((rc = dalloc(c, &p->d_fslabs, size_t(B) * p->V))) return rc;
@@ -524,7 +552,7 @@ int dpm_dmax_sigma(dpm_ctx *c, const int *ids, int n, double *out) {
     }
   }
   if (n > c->dmax_cap) {
-    cudaFree(c->d_dmax_out);
+    dfree(c, c->d_dmax_out);
     c->d_dmax_out = nullptr;
     c->dmax_cap = 0;
     int rc = dalloc(c, &c->d_dmax_out, size_t(3) * size_t(n));
@@ -554,7 +582,7 @@ int dpm_sync(dpm_ctx *c) {
     CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
     if (e & ERR_OVERFLOW) return fail(c, DPM_EQUEUE_OVERFLOW, "particle stack or queue overflow");
     if (e & ERR_TIMEOUT) return fail(c, DPM_ETIMEOUT, "a bounded device wait timed out");
-    return fail(c, DPM_ETIMEOUT, "a particle exceeded the step limit");
+    return fail(c, DPM_ESTEPCAP, "a particle exceeded the step limit");
   }
   return DPM_OK;
 }
@@ -596,7 +624,10 @@ static int read_common(dpm_ctx *c, PhantomState *p, const int64_t *s1_host, dpm_
     }
     cudaGetLastError();
     drop_events(p);
-    st->error_flags = sync_rc == DPM_OK ? 0 : (sync_rc == DPM_EQUEUE_OVERFLOW ? 1 : 4);
+    st->error_flags = sync_rc == DPM_OK                ? 0
+                      : sync_rc == DPM_EQUEUE_OVERFLOW ? 1
+                      : sync_rc == DPM_ESTEPCAP        ? 2
+                                                       : 4;
   }
   return DPM_OK;
 }
@@ -672,7 +703,7 @@ int dpm_diag_table(dpm_ctx *c, int which, int mat, int n, const double *energy, 
   launch_diag_table(c->dt, P, which, mat, n, d, d + n, d + 2 * n, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess) e = cudaMemcpy(out, d + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost);
-  cudaFree(d);
+  dfree(c, d);
   if (e != cudaSuccess) return fail(c, DPM_ECUDA, cudaGetErrorString(e));
   return DPM_OK;
 }
@@ -690,7 +721,7 @@ int dpm_diag_sample(dpm_ctx *c, int which, double e, double aux, int n, const do
   launch_diag_sample(c->dt, which, e, aux, n, d, d + n, c->stream);
   cudaError_t er = cudaStreamSynchronize(c->stream);
   if (er == cudaSuccess) er = cudaMemcpy(out, d + n, n * sizeof(double), cudaMemcpyDeviceToHost);
-  cudaFree(d);
+  dfree(c, d);
   if (er != cudaSuccess) return fail(c, DPM_ECUDA, cudaGetErrorString(er));
   return DPM_OK;
 }
@@ -708,7 +739,7 @@ int dpm_diag_philox(dpm_ctx *c, int n, const uint32_t *ctr, const uint32_t *key,
   launch_diag_philox(n, d, d + 4 * n, d + 6 * n, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess) e = cudaMemcpy(out, d + 6 * n, 4 * n * sizeof(uint32_t), cudaMemcpyDeviceToHost);
-  cudaFree(d);
+  dfree(c, d);
   if (e != cudaSuccess) return fail(c, DPM_ECUDA, cudaGetErrorString(e));
   return DPM_OK;
 }
@@ -725,7 +756,7 @@ int dpm_diag_atomic_replay(dpm_ctx *c, const uint32_t *ids, uint64_t n, uint64_t
   int rc;
   if ((rc = dalloc(c, &slab, size_t(n_vox)))) return rc;
   if ((rc = dalloc(c, &d_ids, size_t(n)))) {
-    cudaFree(slab);
+    dfree(c, slab);
     return rc;
   }
   cudaEvent_t ev[2];
@@ -745,8 +776,8 @@ int dpm_diag_atomic_replay(dpm_ctx *c, const uint32_t *ids, uint64_t n, uint64_t
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
-  cudaFree(slab);
-  cudaFree(d_ids);
+  dfree(c, slab);
+  dfree(c, d_ids);
   if (e != cudaSuccess) return fail(c, DPM_ECUDA, cudaGetErrorString(e));
   *rate = double(n) / (ms * 1e-3);
   return DPM_OK;
@@ -786,7 +817,7 @@ int dpm_diag_l2_peaks(dpm_ctx *c, uint64_t ws_bytes, double *out) {
   if (e == cudaSuccess) e = cudaEventElapsedTime(&t_atom, ev[0], ev[1]);
   if (e == cudaSuccess) e = cudaEventElapsedTime(&t_read, ev[2], ev[3]);
   for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
-  cudaFree(d);
+  dfree(c, d);
   if (e != cudaSuccess) return fail(c, DPM_ECUDA, cudaGetErrorString(e));
   out[0] = double(blocks) * 256.0 * iters / (t_atom * 1e-3);
   out[1] = double(ws_bytes) * passes / (t_read * 1e-3);

@@ -6,6 +6,7 @@
 
 #include <memory>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "dpm_internal.h"
@@ -55,6 +56,10 @@ struct PhantomState {
 
 struct dpm_ctx {
   int device = 0;
+  // device memory the context keeps (every allocation but the 4-byte error
+  // word), against an optional budget (0 = none)
+  uint64_t budget = 0, in_use = 0;
+  std::unordered_map<const void *, size_t> alloc_bytes;
   int sm_count = 0;
   cudaStream_t own = nullptr, stream = nullptr;
   std::string err;
@@ -94,5 +99,8 @@ int ctx_alloc(dpm_ctx *c, void **p, size_t bytes);
 // Batch structure of a run of n histories in (at most) n_batches batches:
 // makes sure the phantom has B slabs and uploads 1/n_b; returns bs and B.
 int ctx_prepare_batches(dpm_ctx *c, PhantomState *p, uint64_t n, int n_batches, uint64_t &bs, int &B);
+// With the context's device current: load the module holding the scratch of
+// dpm_run_noalloc() and the queue kernels (dpm_noalloc.cu).
+int noalloc_setup(std::string &err);
 
 }  // namespace dpm

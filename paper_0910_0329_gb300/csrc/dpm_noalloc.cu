@@ -12,7 +12,8 @@
 // caller owns.  It calls no cudaMalloc, cudaFree or other allocating routine.
 #include <cuda_runtime.h>
 
-#include <mutex>
+#include <cmath>
+#include <cstring>
 #include <string>
 
 #include "dpm_ctx.h"
@@ -23,47 +24,55 @@ namespace dpm {
 namespace {
 
 // Scratch of dpm_run_noalloc(): particle queues plus a 256-byte header
-// (run counters and the error word).  Every GPU that loads the library holds
-// this array until the process exits.
+// (run counters and the error word).  The driver places it in a device's
+// memory when it loads this file's module there; noalloc_setup() makes that
+// happen in dpm_create(), and the array stays until the process exits.
 constexpr size_t kNoAllocBytes = size_t(DPM_NOALLOC_SCRATCH_BYTES);
 constexpr size_t kHeader = 256;
 constexpr int kNoAllocLog2Slots = 9;  // 512 slots per queue shard
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// In host code g_noalloc_scratch is only a host-side stand-in; the device
-// address is looked up once per device with that device current.
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
-
-int scratch_address(int dev, void **out, std::string &err) {
-  if (dev < 0 || dev >= kMaxDevices) {
-    err = "device index out of range";
-    return DPM_EINVAL;
+// In host code g_noalloc_scratch is only a host-side stand-in: the device
+// address is looked up with the device current.  The lookup is repeated on
+// every call (it is cheap once the module is loaded), so that a new primary
+// context on the device never leaves a stale address behind.
+int scratch_address(void **out, std::string &err) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+    return DPM_ECUDA;
   }
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-      return DPM_ECUDA;
-    }
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return DPM_OK;
 }
 
 }  // namespace
+
+// Called by dpm_create() with the context's device current: loads this
+// module (placing the scratch array in device memory) and the queue kernels,
+// so that later dpm_run_noalloc() calls find everything resident.
+int noalloc_setup(std::string &err) {
+  void *p = nullptr;
+  const int rc = scratch_address(&p, err);
+  if (rc) return rc;
+  if (queue_preload() < 1) {
+    err = "queue kernel load failed";
+    return DPM_ECUDA;
+  }
+  return DPM_OK;
+}
+
 }  // namespace dpm
 
 using namespace dpm;
 
 extern "C" int dpm_run_noalloc(dpm_ctx *c, int phantom_id, const dpm_source *src, uint64_t first_history,
-                               uint64_t n_histories, uint64_t seed, int64_t *d_tally) {
+                               uint64_t n_histories, uint64_t seed, int64_t *d_tally, dpm_run_stats *stats) {
   if (!c) return DPM_EINVAL;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
   PhantomState *p = ctx_phantom(c, phantom_id);
   if (!p) return ctx_fail(c, DPM_EINVAL, "bad phantom id");
   if (!d_tally) return ctx_fail(c, DPM_EINVAL, "null tally");
@@ -74,10 +83,9 @@ extern "C" int dpm_run_noalloc(dpm_ctx *c, int phantom_id, const dpm_source *src
   if (n_histories == 0) return DPM_OK;
   if (cudaSetDevice(c->device) != cudaSuccess) return ctx_fail(c, DPM_ECUDA, "cudaSetDevice failed");
 
-  // first call on this device: resolve the scratch array's device address
   void *base = nullptr;
   std::string err;
-  if ((rc = scratch_address(c->device, &base, err))) return ctx_fail(c, rc, err);
+  if ((rc = scratch_address(&base, err))) return ctx_fail(c, rc, err);
 
   // shards that fit in the scratch, at most one per resident block
   const int per_sm = queue_blocks_per_sm();
@@ -99,15 +107,34 @@ extern "C" int dpm_run_noalloc(dpm_ctx *c, int phantom_id, const dpm_source *src
                          err)))
     return ctx_fail(c, rc, err);
 
-  // wait, then report the device-side status of this call
+  // wait, then report the device-side status and counters of this call
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
     const cudaError_t e = cudaGetLastError();
     return ctx_fail(c, DPM_ECUDA, std::string("transport failed: ") + cudaGetErrorString(e));
   }
+  unsigned long long cnt[kCounterSlots];
   int dev_err = 0;
-  if (cudaMemcpy(&dev_err, hdr + 128, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (cudaMemcpy(cnt, hdr, sizeof(cnt), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&dev_err, hdr + 128, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return ctx_fail(c, DPM_ECUDA, "status read failed");
+  if (stats) {
+    stats->n_histories = n_histories;
+    stats->n_batches = 1;
+    stats->error_flags = dev_err;
+    stats->emitted = double((long long)cnt[C_EMIT]) / kCounterScale;
+    stats->escaped = double((long long)cnt[C_ESC]) / kCounterScale;
+    stats->missed = double((long long)cnt[C_MISS]) / kCounterScale;
+    stats->deposited = std::nan("");  // the tally is the caller's: deposited = its increase * 2^-32 MeV
+    stats->n_e_steps = cnt[C_ESTEP];
+    stats->n_g_flights = cnt[C_GFLIGHT];
+    stats->n_g_interactions = cnt[C_GINT];
+    stats->n_tally_atomics = cnt[C_ATOM];
+    stats->n_pushed = cnt[C_PUSH];
+    stats->n_transport_launches = 1;
+    stats->n_phase_switches = cnt[C_SWITCH];
+  }
   if (dev_err & ERR_OVERFLOW) return ctx_fail(c, DPM_EQUEUE_OVERFLOW, "particle queue overflow in the fixed scratch");
-  if (dev_err) return ctx_fail(c, DPM_ETIMEOUT, "a bounded device wait timed out");
+  if (dev_err & ERR_TIMEOUT) return ctx_fail(c, DPM_ETIMEOUT, "a bounded device wait timed out");
+  if (dev_err & ERR_STEPCAP) return ctx_fail(c, DPM_ESTEPCAP, "a particle exceeded the step limit");
   return DPM_OK;
 }

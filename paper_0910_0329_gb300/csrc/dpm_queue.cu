@@ -654,6 +654,17 @@ int queue_blocks_per_sm() {
   return std::min(per_sm, per_sm_multi);
 }
 
+int queue_preload() {
+  // cudaFuncGetAttributes loads a kernel under lazy module loading
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, k_queue<false>) != cudaSuccess || cudaFuncGetAttributes(&a, k_queue<true>) != cudaSuccess ||
+      cudaFuncGetAttributes(&a, k_queue_init) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return queue_blocks_per_sm();
+}
+
 constexpr int kWordsPerSlot = 13;  // x y z u v w E, voxel, id lo, id hi, history, job, sequence
 constexpr int kCtlWords = 8 + kMaxJobs;  // next_hist idle started cur_job[2] backlog[2] phase, job_next[kMaxJobs]
 
@@ -747,7 +758,13 @@ int queue_prepare(QueueState &q, const dpm_run_opts &o, int sm_count, int &K, in
   }
   const size_t bytes = queue_bytes(K, log2cs);
   if (q.bytes < bytes) {
+    if (q.budget && q.in_use && *q.in_use - q.bytes + bytes > q.budget) {
+      err = "device-memory budget of the context exceeded by the particle queues (" + std::to_string(bytes) +
+            " bytes)";
+      return DPM_ENOMEM;
+    }
     if (q.mem) cudaFree(q.mem);
+    if (q.in_use) *q.in_use -= q.bytes;
     q.mem = nullptr;
     q.bytes = 0;
     cudaError_t e = cudaMalloc(&q.mem, bytes);
@@ -757,6 +774,7 @@ int queue_prepare(QueueState &q, const dpm_run_opts &o, int sm_count, int &K, in
       return DPM_ENOMEM;
     }
     q.bytes = bytes;
+    if (q.in_use) *q.in_use += bytes;
   }
   q.log2_cap = log2cs;
   return DPM_OK;
@@ -780,6 +798,7 @@ int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_
 
 void queue_free(QueueState &q) {
   if (q.mem) cudaFree(q.mem);
+  if (q.in_use) *q.in_use -= q.bytes;
   q.mem = nullptr;
   q.bytes = 0;
 }

@@ -13,6 +13,8 @@ struct QueueState {
   void *mem = nullptr;     // one device allocation holding queues and control words
   size_t bytes = 0;
   int log2_cap = 0;
+  uint64_t budget = 0;          // the owning context's device-memory budget (0 = none)
+  uint64_t *in_use = nullptr;   // the owning context's bytes in use (the queues' included)
 };
 
 // Launch the persistent kernel for one run; returns a dpm_status code.
@@ -27,6 +29,10 @@ int queue_prepare(QueueState &q, const dpm_run_opts &o, int sm_count, int &K, in
 
 // Resident blocks per SM of the queue kernel (occupancy query), or 0 on error.
 int queue_blocks_per_sm();
+// Load the queue kernels on the current device now (they are otherwise
+// loaded at their first launch under lazy module loading); returns
+// queue_blocks_per_sm(), or 0 on error.
+int queue_preload();
 // Device bytes the queues of K shards of 2^log2cs slots occupy.
 size_t queue_bytes(int K, int log2cs);
 // Lay the queues out in caller-provided device memory `mem` (at least

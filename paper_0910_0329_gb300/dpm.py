@@ -19,10 +19,11 @@ from . import workloads as W
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libdpm.so")
 
 DPM_OK, DPM_EINVAL, DPM_ENOMEM, DPM_ECUDA, DPM_EQUEUE_OVERFLOW, DPM_ETIMEOUT, DPM_ESTATE = 0, -1, -2, -3, -4, -5, -6
+DPM_ESTEPCAP = -7
 KERNEL_QUEUE, KERNEL_HISTORY, KERNEL_PAPER_F32, KERNEL_PAPER_CAS = 0, 1, 2, 3
 NO_HARD, NO_MSC = 1, 2
 _NAMES = {0: "DPM_OK", -1: "DPM_EINVAL", -2: "DPM_ENOMEM", -3: "DPM_ECUDA", -4: "DPM_EQUEUE_OVERFLOW",
-          -5: "DPM_ETIMEOUT", -6: "DPM_ESTATE"}
+          -5: "DPM_ETIMEOUT", -6: "DPM_ESTATE", -7: "DPM_ESTEPCAP"}
 
 
 class DpmError(RuntimeError):
@@ -92,7 +93,8 @@ class dpm_run_stats(C.Structure):
 # Every symbol declared in include/dpm.h with its ctypes signature.
 _P = C.c_void_p
 _SIGS = {
-    "dpm_create": (C.c_int, [C.POINTER(_P), C.c_int]),
+    "dpm_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_uint64]),
+    "dpm_device_bytes": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "dpm_destroy": (None, [_P]),
     "dpm_last_error": (C.c_char_p, [_P]),
     "dpm_set_stream": (C.c_int, [_P, _P]),
@@ -116,7 +118,8 @@ _SIGS = {
     "dpm_diag_philox": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "dpm_diag_l2_peaks": (C.c_int, [_P, C.c_uint64, _P]),
     "dpm_diag_atomic_replay": (C.c_int, [_P, _P, C.c_uint64, C.c_uint64, _P]),
-    "dpm_run_noalloc": (C.c_int, [_P, C.c_int, C.POINTER(dpm_source), C.c_uint64, C.c_uint64, C.c_uint64, _P]),
+    "dpm_run_noalloc": (C.c_int, [_P, C.c_int, C.POINTER(dpm_source), C.c_uint64, C.c_uint64, C.c_uint64, _P,
+                                  C.POINTER(dpm_run_stats)]),
     "dpm_server_create": (C.c_int, [_P, C.POINTER(dpm_serve_opts), C.POINTER(_P)]),
     "dpm_server_destroy": (None, [_P]),
     "dpm_server_submit": (C.c_int, [_P, C.c_int, C.POINTER(dpm_source), C.c_uint64, C.POINTER(C.c_int)]),
@@ -168,11 +171,18 @@ def _ptr(a: np.ndarray):
 # ---------------------------------------------------------------------------
 # ABI-named wrappers
 # ---------------------------------------------------------------------------
-def dpm_create(device: int = 0):
+def dpm_create(device: int = 0, hbm_budget_bytes: int = 0):
     h = _P()
-    rc = lib().dpm_create(C.byref(h), device)
+    rc = lib().dpm_create(C.byref(h), device, hbm_budget_bytes)
     _check(None, rc)
     return h
+
+
+def dpm_device_bytes(ctx):
+    """(bytes of device memory the context holds, its budget; 0 = none)."""
+    used, budget = C.c_uint64(), C.c_uint64()
+    _check(ctx, lib().dpm_device_bytes(ctx, C.byref(used), C.byref(budget)))
+    return used.value, budget.value
 
 
 def dpm_destroy(ctx):
@@ -414,8 +424,8 @@ def dpm_batch_stats(ctx) -> dict:
 class Dpm:
     """Convenience wrapper: one context, tables built from a parameter dict."""
 
-    def __init__(self, device=0, materials=None, params=None, stream=None):
-        self.ctx = dpm_create(device)
+    def __init__(self, device=0, materials=None, params=None, stream=None, hbm_budget_bytes=0):
+        self.ctx = dpm_create(device, hbm_budget_bytes)
         if stream is not None:
             dpm_set_stream(self.ctx, stream)
         self.phantoms = {}
@@ -508,9 +518,13 @@ class HostTables:
             pass
 
 
-def dpm_run_noalloc(ctx, pid: int, src: W.Source, first: int, n: int, seed: int, d_tally_ptr: int):
+def dpm_run_noalloc(ctx, pid: int, src: W.Source, first: int, n: int, seed: int, d_tally_ptr: int) -> dict:
     """Transport into a caller-owned device int64 tally without allocating
     device memory (the fixed-scratch entry point); ``d_tally_ptr`` is a raw
-    device pointer, e.g. ``tensor.data_ptr()`` of a CUDA int64 tensor."""
+    device pointer, e.g. ``tensor.data_ptr()`` of a CUDA int64 tensor.
+    Returns the run's counters (``deposited`` is NaN: it is the tally's
+    increase)."""
     s = source_struct(src)
-    _check(ctx, lib().dpm_run_noalloc(ctx, pid, C.byref(s), first, n, seed, _P(d_tally_ptr)))
+    st = dpm_run_stats()
+    _check(ctx, lib().dpm_run_noalloc(ctx, pid, C.byref(s), first, n, seed, _P(d_tally_ptr), C.byref(st)))
+    return st.as_dict()

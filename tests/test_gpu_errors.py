@@ -117,3 +117,40 @@ def test_energy_counters_do_not_wrap_on_large_runs():
     assert raw.sum() == 0 and st["error_flags"] == 0
     assert st["emitted"] == pytest.approx(4.0e9, rel=1e-6)
     assert st["missed"] == st["emitted"]
+
+
+def test_device_memory_budget_of_a_context(gpu_lib):
+    """dpm_create's budget: allocations are counted (and released by frees),
+    one that would pass the budget fails with DPM_ENOMEM before cudaMalloc,
+    and the context stays usable."""
+    wl = W.c0_electron_wlw()
+    with dpm.Dpm(0, W.MATERIALS, wl.params) as d:
+        used0, budget0 = dpm.dpm_device_bytes(d.ctx)
+        assert budget0 == 0 and used0 > 0  # the tables
+        pid = d.load_phantom(wl.phantom)
+        used1, _ = dpm.dpm_device_bytes(d.ctx)
+        V = wl.phantom.n_vox
+        assert used1 - used0 >= V * (1 + 4 + 8 + 8)  # mat, rho, S1, Q
+        d.run(pid, wl.source, 2000, wl.seed)
+        d.read(pid)
+        used_run, _ = dpm.dpm_device_bytes(d.ctx)
+        need = used_run  # tables + phantom + slabs + queues of one run
+        dpm.dpm_free_phantom(d.ctx, pid)
+        used2, _ = dpm.dpm_device_bytes(d.ctx)
+        assert used2 < used_run - V * (1 + 4 + 8 + 8)
+    # a budget below what one run needs: the run fails with DPM_ENOMEM, a
+    # second phantom load too, and the first phantom's tally is intact
+    with dpm.Dpm(0, W.MATERIALS, wl.params, hbm_budget_bytes=need // 2) as d:
+        assert dpm.dpm_device_bytes(d.ctx)[1] == need // 2
+        try:
+            pid = d.load_phantom(wl.phantom)
+        except dpm.DpmError as e:
+            assert e.code == dpm.DPM_ENOMEM
+        else:
+            assert code_of(d.run, pid, wl.source, 2000, wl.seed) == dpm.DPM_ENOMEM
+        assert dpm.dpm_device_bytes(d.ctx)[0] <= need // 2
+    # a budget that fits: the same run goes through
+    with dpm.Dpm(0, W.MATERIALS, wl.params, hbm_budget_bytes=need + (1 << 20)) as d:
+        pid = d.load_phantom(wl.phantom)
+        d.run(pid, wl.source, 2000, wl.seed)
+        assert d.read(pid)[2].sum() > 0
