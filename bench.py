@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--histories", type=int, default=0, help="histories per step (default: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-target", action="store_true",
+                    help="skip the measured time to 1 %% sigma (profiling runs of small steps)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU work of the oracle baseline sample")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="history scale of the batch64 workload")
     ap.add_argument("--autotune", action="store_true", help="tune the batched launch before timing it")
@@ -130,6 +132,30 @@ def profiled_traffic(kernel: str, workload: str, key: str = "traffic_bytes_per_h
     if not fp or not tb:
         return None
     return float(tb.group(1)) if kernel_fingerprint(kernel) == fp.group(1) else None
+
+
+SM_COUNT, SCHEDULERS_PER_SM = 152, 4
+
+
+def issue_roofline(kernel: str, workload: str, hist_per_s: float):
+    """Instruction-issue view of the kernel: warp instructions per history
+    (from the committed ncu capture, if it matches the kernel's source) times
+    the measured histories/s, against the issue ceiling of one warp
+    instruction per scheduler per cycle at the maximum SM clock."""
+    wph = profiled_traffic(kernel, workload, "warp_inst_per_history")
+    issue = profiled_traffic(kernel, workload, "issue_active_pct")
+    mhz = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = json.load(f).get("sm_max_mhz")
+    mhz = mhz or 2070.0
+    peak = SM_COUNT * SCHEDULERS_PER_SM * mhz * 1e6
+    ach = wph * hist_per_s if wph else None
+    return {"achieved": ach, "peak": peak, "unit": "warp instructions/s", "frac": ach / peak if ach else None,
+            "warp_inst_per_history": wph, "issue_active_pct_ncu": issue,
+            "what": "warp instructions per history (ncu smsp__inst_executed.sum of the committed capture / its "
+                    "histories) x histories/s, against 4 issue slots per SM per cycle at the maximum SM clock"}
 
 
 def time_to_target(d, pid, wl, chunk, kernel, target=0.01, max_chunks=200):
@@ -341,6 +367,13 @@ def main():
     dose, sigma, raw, st = d.read(pid)
     n_tot = n * args.steps
     value = world * n_tot / (tot_ms / 1000.0)
+    # event counts (tally atomics, secondaries) for the roofline: one more
+    # step with counting on, after the timed region (the timed steps do not
+    # count events, see dpm_run_opts.count_events); same histories, same tally
+    d.reset(pid)
+    d.run(pid, wl.source, n, wl.seed, first=sharding.history_range(rank, world, 0, n)[0], kernel=kernel,
+          count_events=1)
+    st_cnt = d.read(pid)[3]
 
     # statistical efficiency: sigma at D_max after n_tot histories -> time to 1 %
     imax = int(np.argmax(dose))
@@ -356,17 +389,16 @@ def main():
     peak, peak_kind = measured_peaks()
     t_kernel_s = st["transport_ms"] / 1000.0 / max(st["n_transport_launches"], 1)
     hist_per_launch = n
-    atom_per_hist = st["n_tally_atomics"] / n_tot
-    sec_per_hist = st["n_pushed"] / n_tot
+    atom_per_hist = st_cnt["n_tally_atomics"] / n
+    sec_per_hist = st_cnt["n_pushed"] / n
     bytes_per_hist = 8 * atom_per_hist + 88 * sec_per_hist + 44
     achieved = bytes_per_hist * hist_per_launch / t_kernel_s / 1e9
     kname = KERNELS[args.kernel][1]
     tph = profiled_traffic(kname, args.workload)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": tph * hist_per_launch if tph else None, "peak_kind": peak_kind, "kernel": kname,
-            "kernel_ms_per_launch": t_kernel_s * 1000, "bytes_per_history": bytes_per_hist,
-            "tally_atomics_per_history": atom_per_hist, "secondaries_per_history": sec_per_hist,
-            "kernel_share_of_step": st["transport_ms"] / max(tot_ms, 1e-9)}
+    hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+           "bytes_per_history": bytes_per_hist,
+           "what": "algorithmic bytes (8 B per tally atomic, 88 B per queued secondary, 44 B per primary) per "
+                   "launch / the launch's event time, against the measured HBM copy bandwidth"}
 
     # queue init + transport + fold; transport + fold; transport + float rounding + fold
     launches_per_step = {"queue": 3, "history": 2}.get(args.kernel, 3)
@@ -379,7 +411,7 @@ def main():
                        "parallelism": f"{world} replica(s), disjoint history ranges"},
             "time_to_1pct_sigma_at_dmax_s": t_1pct, "sigma_rel_at_dmax": rel, "histories_accumulated": n_tot * world,
             "mean_sigma_rel_above_half_dmax": mean_rel_50,
-            "roofline": roof, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk, "gpu_launches": launches_per_step * args.steps,
             "wall_s_timed_region": wall,
             "energy_balance_rel": abs(st["emitted"] - st["deposited"] - st["escaped"] - st["missed"]) / st["emitted"]}
 
@@ -393,13 +425,24 @@ def main():
     replay_pk = dpm.dpm_diag_atomic_replay(d.ctx, deposit_stream(raw, 1 << 24), ph.n_vox)
     l2_bph = profiled_traffic(kname, args.workload, "l2_bytes_per_history")
     l2_rate = l2_bph * hist_per_launch / t_kernel_s if l2_bph else None
+    # headline: the tally-atomic roofline of the scope (achieved tally atomics
+    # per second against the replayed ceiling of the same address stream)
+    line["roofline"] = {
+        "bound": "l2_atomic_replay", "achieved": atom_rate, "peak": replay_pk, "unit": "atomics/s",
+        "frac": atom_rate / replay_pk, "traffic": tph * hist_per_launch if tph else None,
+        "peak_kind": "measured live (dpm_diag_atomic_replay: 2^24 voxel ids drawn from this run's tally, issued "
+                     "as 64-bit atomic adds at full occupancy)",
+        "kernel": kname, "kernel_ms_per_launch": t_kernel_s * 1000, "histories_per_launch": hist_per_launch,
+        "tally_atomics_per_history": atom_per_hist, "secondaries_per_history": sec_per_hist,
+        "kernel_share_of_step": st["transport_ms"] / max(tot_ms, 1e-9),
+        "traffic_what": "dram__bytes_read.sum + dram__bytes_write.sum per launch, scaled from the committed ncu "
+                        "capture's bytes per history (null if the kernel changed since)",
+        "hbm": hbm,
+        "issue": issue_roofline(kname, args.workload, value / world),
+    }
     line["l2_roofline"] = {
         "atomics": {"achieved": atom_rate, "peak": atom_pk, "unit": "atomics/s", "frac": atom_rate / atom_pk,
                     "what": "tally atomics of the transport kernel vs scattered 64-bit atomics over 16 MiB"},
-        "atomics_replay": {"achieved": atom_rate, "peak": replay_pk, "unit": "atomics/s",
-                           "frac": atom_rate / replay_pk,
-                           "what": "tally atomics vs the same phantom's deposit address distribution (2^24 ids "
-                                   "drawn from this run's tally) replayed as 64-bit atomic adds"},
         "bandwidth": {"achieved": l2_rate / 1e9 if l2_rate else None, "peak": l2_pk / 1e9, "unit": "GB/s",
                       "frac": l2_rate / l2_pk if l2_rate else None, "bytes_per_history": l2_bph,
                       "what": "L1->L2 sectors per history (ncu capture of this kernel) vs L1-bypassing loads "
@@ -409,7 +452,8 @@ def main():
     # time to 1 % sigma at D_max, measured: chunks of the step's histories
     # with a device-side check of sigma/D at D_max after each (the serving
     # loop's stop rule), from a fresh tally
-    line["time_to_1pct_sigma_at_dmax_measured"] = time_to_target(d, pid, wl, n, kernel)
+    if not args.no_time_to_target:
+        line["time_to_1pct_sigma_at_dmax_measured"] = time_to_target(d, pid, wl, n, kernel)
 
     if not args.no_e2e:
         line["e2e"] = e2e(args, d, wl, n, kernel, local, rank, world)

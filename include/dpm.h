@@ -119,6 +119,11 @@ typedef struct {
                           a push that finds no shard below it is an overflow */
     int use_graph;     /* dpm_run_batch only: capture zero -> transport -> fold in a CUDA
                           graph and replay it while the batch keeps its shape */
+    int count_events;  /* queue kernel: 1 = also count electron steps, photon flights and
+                          interactions, tally atomics and secondaries for dpm_run_stats
+                          (about 10 % slower); 0 = those counts read 0.  The energy
+                          counters and the tally are the same either way.  The per-history
+                          kernels always count. */
 } dpm_run_opts;
 enum { DPM_NO_HARD = 1, DPM_NO_MSC = 2 };
 
@@ -416,7 +421,9 @@ int dpm_diag_atomic_replay(dpm_ctx *ctx, const uint32_t *ids, uint64_t n, uint64
    untouched).  stats (host, may be NULL) receives the run's counters
    (emitted, escaped and missed energy, steps, flights, atomics, pushes, error
    flags) with `deposited` set to NaN: the deposited energy is the increase of
-   the caller's d_tally times 2^-32 MeV. */
+   the caller's d_tally times 2^-32 MeV.  With stats given the kernel also
+   counts events (dpm_run_opts.count_events), about 10 % slower; the tally is
+   the same either way. */
 #define DPM_NOALLOC_SCRATCH_BYTES (48u << 20)
 int dpm_run_noalloc(dpm_ctx *ctx, int phantom_id, const dpm_source *src, uint64_t first_history,
                     uint64_t n_histories, uint64_t seed, int64_t *d_tally, dpm_run_stats *stats);

@@ -375,9 +375,32 @@ int dpm_build_tables(dpm_ctx *c, const dpm_material *mats, int n_mat, const dpm_
   d.n_e = t.n_e;
   d.lnE_lo = float(std::log(t.e_lo));
   d.inv_dlnE = float((t.n_e - 1) / (std::log(t.e_hi) - std::log(t.e_lo)));
+  {
+    const double inv = (t.n_e - 1) / (std::log(t.e_hi) - std::log(t.e_lo));
+    d.x_lg2 = float(inv * std::log(2.0));
+    d.x_lo = float(-std::log(t.e_lo) * inv);
+  }
   int rc;
   const float *ph, *el;
-  if ((rc = upload(c, t.ph, &ph)) || (rc = upload(c, t.el, &el)) || (rc = upload(c, t.pmol, &d.pmol))) return rc;
+  // device layout of the float4 tables: each node's value followed by the
+  // float difference to the next node (see el_at in dpm_device.cuh)
+  auto with_steps = [&](const std::vector<float> &h) {
+    std::vector<float> o(2 * h.size(), 0.f);
+    for (int m = 0; m < t.n_mat; ++m)
+      for (int i = 0; i < t.n_e; ++i)
+        for (int k = 0; k < 4; ++k) {
+          const size_t at = (size_t(m) * t.n_e + i) * 4 + k;
+          o[2 * at - k] = h[at];
+          if (i + 1 < t.n_e) {
+            volatile float diff = h[at + 4] - h[at];  // one float subtraction, as on the device
+            o[2 * at - k + 4] = diff;
+          }
+        }
+    return o;
+  };
+  if ((rc = upload(c, with_steps(t.ph), &ph)) || (rc = upload(c, with_steps(t.el), &el)) ||
+      (rc = upload(c, t.pmol, &d.pmol)))
+    return rc;
   d.ph = reinterpret_cast<const float4 *>(ph);
   d.el = reinterpret_cast<const float4 *>(el);
   auto samp = [&](const std::vector<float> &v, int ne, double lo, double hi, SampTab &s) {

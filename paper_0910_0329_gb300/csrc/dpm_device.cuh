@@ -56,8 +56,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
-// uniform in the open interval (0, 1) from the top 24 bits
-__device__ __forceinline__ float u01(uint32_t x) { return (float(x >> 8) + 0.5f) * (1.0f / 16777216.0f); }
+// uniform on (0, 1] from the top 24 bits: (k + 1/2) 2^-24 for k = x >> 8, in
+// one rounding (the top values round to 1)
+__device__ __forceinline__ float u01(uint32_t x) {
+  return fmaf(float(x >> 8), 1.0f / 16777216.0f, 1.0f / 33554432.0f);
+}
 
 // -ln(u) for an exponential free path, with the hardware logarithm (absolute
 // error about 2^-21 near u = 1, far below the paths' statistical spread); the
@@ -127,8 +130,8 @@ __device__ __forceinline__ int vox(const Part &p, const DevPhantom &P) { return 
 // suffices: a step that reaches a face puts the coordinate on the face
 // exactly (cross_face), so its error only moves the step length by 2 ulp.
 __device__ __forceinline__ float face_dist(float x, float u, int i, float d) {
-  if (u > 0.f) return fmaxf(__fdividef(float(i + 1) * d - x, u), 0.f);
-  if (u < 0.f) return fmaxf(__fdividef(float(i) * d - x, u), 0.f);
+  if (u > 0.f) return fmaxf(__fdividef(fmaf(float(i + 1), d, -x), u), 0.f);
+  if (u < 0.f) return fmaxf(__fdividef(fmaf(float(i), d, -x), u), 0.f);
   return kInf;
 }
 
@@ -174,12 +177,12 @@ __device__ __forceinline__ void locate(Part &p, const DevPhantom &P) {
 // accurate to about 2^-21 absolute; the direction is renormalised below.
 __device__ __forceinline__ void rotate(float &u, float &v, float &w, float c, float h) {
   c = fminf(fmaxf(c, -1.f), 1.f);
-  const float c2 = fmaxf(0.f, 1.f - c * c);
+  const float c2 = fmaxf(0.f, fmaf(-c, c, 1.f));
   const float s = c2 * rsqrtf(fmaxf(c2, 1e-30f));  // sin(theta) by the hardware 1/sqrt
   float sp, cp;
   const float t = h - 2.f * floorf(0.5f * h + 0.5f);  // h modulo 2, in [-1, 1)
   __sincosf(3.14159265f * t, &sp, &cp);
-  const float r2 = u * u + v * v;
+  const float r2 = fmaf(u, u, v * v);
   float nu, nv, nw;
   if (r2 < 1e-10f) {
     nu = s * cp;
@@ -187,11 +190,11 @@ __device__ __forceinline__ void rotate(float &u, float &v, float &w, float c, fl
     nw = (w >= 0.f) ? c : -c;
   } else {
     const float ir = rsqrtf(r2), r = r2 * ir, a = s * ir;  // hardware 1/sqrt; renormalised below
-    nu = u * c + a * (u * w * cp - v * sp);
-    nv = v * c + a * (v * w * cp + u * sp);
-    nw = w * c - s * r * cp;
+    nu = fmaf(u, c, a * fmaf(u * w, cp, -(v * sp)));
+    nv = fmaf(v, c, a * fmaf(v * w, cp, u * sp));
+    nw = fmaf(w, c, -(s * r) * cp);
   }
-  const float n = rsqrtf(nu * nu + nv * nv + nw * nw);
+  const float n = rsqrtf(fmaf(nu, nu, fmaf(nv, nv, nw * nw)));
   u = nu * n;
   v = nv * n;
   w = nw * n;
@@ -214,12 +217,16 @@ __device__ __forceinline__ EIdx eidx_x(const DevTables &T, float x) {
   return e;
 }
 
-// Grid position of energy E.  The hardware logarithm (within 7.2e-7 of ln E
-// on the tables' range, the intrinsic's documented bound) moves the position
-// by at most 2.5e-4 of a node spacing at 2048 nodes: an interpolation error
-// well below the tables' own.
+// Fractional node index of energy E on the uniform ln E grid, from the
+// hardware base-2 logarithm in one FMA (x_lg2 = ln 2 / spacing, x_lo = -ln E_lo
+// / spacing).  The intrinsic's documented error (2 ulp of log2 E, within
+// 7e-7 of ln E on the tables' range) moves the position by at most 2.5e-4 of
+// a node spacing at 2048 nodes: an interpolation error well below the
+// tables' own.
+__device__ __forceinline__ float egrid(const DevTables &T, float E) { return fmaf(__log2f(E), T.x_lg2, T.x_lo); }
+
 __device__ __forceinline__ EIdx eidx(const DevTables &T, float E) {
-  float x = (__logf(E) - T.lnE_lo) * T.inv_dlnE;
+  float x = egrid(T, E);
   x = fminf(fmaxf(x, 0.f), float(T.n_e - 1) - 1e-3f);
   EIdx e;
   e.i = int(x);
@@ -233,14 +240,34 @@ __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float f) {
   return make_float4(lerp(a.x, b.x, f), lerp(a.y, b.y, f), lerp(a.z, b.z, f), lerp(a.w, b.w, f));
 }
 
+// The per-material float4 tables hold, for every node, its value and the
+// difference to the next node (a 32-byte record): one interpolation reads one
+// aligned sector and takes one FMA per component, with the same result as
+// interpolating between the two nodes (the difference is the same float
+// subtraction, done when the table is uploaded).
+__device__ __forceinline__ float4 lerp_node(const float4 *b, float f) {
+  const float4 v = __ldg(b), d = __ldg(b + 1);
+  return make_float4(fmaf(f, d.x, v.x), fmaf(f, d.y, v.y), fmaf(f, d.z, v.z), fmaf(f, d.w, v.w));
+}
+
+__device__ __forceinline__ float lerp_node_x(const float4 *b, float f) {
+  return fmaf(f, __ldg(&b[1].x), __ldg(&b[0].x));
+}
+
 __device__ __forceinline__ float4 el_at(const DevTables &T, int m, EIdx e) {
-  const float4 *b = T.el + size_t(m) * T.n_e + e.i;
-  return lerp4(__ldg(b), __ldg(b + 1), e.f);
+  return lerp_node(T.el + 2 * (size_t(m) * T.n_e + e.i), e.f);
+}
+
+__device__ __forceinline__ float el_range(const DevTables &T, int m, EIdx e) {
+  return lerp_node_x(T.el + 2 * (size_t(m) * T.n_e + e.i), e.f);
 }
 
 __device__ __forceinline__ float4 ph_at(const DevTables &T, int m, EIdx e) {
-  const float4 *b = T.ph + size_t(m) * T.n_e + e.i;
-  return lerp4(__ldg(b), __ldg(b + 1), e.f);
+  return lerp_node(T.ph + 2 * (size_t(m) * T.n_e + e.i), e.f);
+}
+
+__device__ __forceinline__ float ph_mu(const DevTables &T, int m, EIdx e) {
+  return lerp_node_x(T.ph + 2 * (size_t(m) * T.n_e + e.i), e.f);
 }
 
 __device__ __forceinline__ float samp(const SampTab &t, float lnE, float u) {
@@ -264,7 +291,7 @@ __device__ __forceinline__ float msc_A(const DevTables &T, float x) {
   // 1e-7 relative), the hardware exponential above (2 ulp of exp(-x), at
   // most 3e-6 of q); the hardware logarithm then moves the table position
   // by a few 1e-6
-  const float q = x < 0.1f ? x * (1.f - x * (0.5f - x * (1.f / 6.f - x * (1.f / 24.f)))) : 1.f - __expf(-x);
+  const float q = x < 0.1f ? x * fmaf(-x, fmaf(-x, fmaf(-x, 1.f / 24.f, 1.f / 6.f), 0.5f), 1.f) : 1.f - __expf(-x);
   const float lg = __logf(q) + x;
   const float t = (lg - T.msc_x0) * T.msc_inv_dx;
   float lA;
@@ -291,9 +318,9 @@ __device__ __forceinline__ float msc_sample(float A, float xi) { return __fdivid
 // electron's critical path) measured 2-4 % slower.
 __device__ __forceinline__ float csda_energy(const DevTables &T, int m, float T0, float R0, float S0, float mp) {
   const float Rt = R0 - mp;
-  const float T1 = fmaxf(T0 - mp * S0, 0.5f * T0);
+  const float T1 = fmaxf(fmaf(-mp, S0, T0), 0.5f * T0);
   const float4 r = el_at(T, m, eidx(T, T1));
-  return fminf(T1 - (r.x - Rt) * r.y, T0);
+  return fminf(fmaf(-(r.x - Rt), r.y, T1), T0);
 }
 
 // Synthetic 6 MV spectrum f(E) ~ (1 - E/6) E^-1/2 on [0.25, 6] MeV: the CDF in
@@ -497,7 +524,7 @@ __device__ bool photon_segment(Part &p, const Ctx &R, Sink &s, int max_draws = k
       locate(p, P);
       const int v = vox(p, P);
       const int m = P.mat[v];
-      const float mu = P.rho[v] * ph_at(T, m, e).x;
+      const float mu = P.rho[v] * ph_mu(T, m, e);
       if (ua * mumax < mu) {
         s.count_interaction();
         return photon_interact(p, R, s, e, m);
@@ -565,11 +592,11 @@ __device__ bool electron_step(Part &p, const Ctx &R, Sink &s) {
   const float T0 = p.E;
   // on the ln(E) grid the step's end energy (1 - f_e) T0, or eabs_e, lies a
   // fixed shift below T0's position: one logarithm serves both lookups
-  float x0 = (__logf(T0) - T.lnE_lo) * T.inv_dlnE;
+  float x0 = egrid(T, T0);
   const float xe = fmaxf(x0 + T.x_fe, T.x_eabs);
   const float Tend = fmaxf((1.f - T.f_e) * T0, T.eabs_e);
   const float4 r0 = el_at(T, m, eidx_x(T, x0));  // R, S, Sigma_hard, 1/lambda1
-  const float Rend = el_at(T, m, eidx_x(T, xe)).x;
+  const float Rend = el_range(T, m, eidx_x(T, xe));
   const float sE = __fdividef(fmaxf(r0.x - Rend, 0.f), rho);  // path lengths: hardware division (2 ulp)
   const uint4 rn = draw(p, R);
   const float sh = (r0.z > 0.f && !(T.flags & DPM_NO_HARD)) ? __fdividef(neglog(u01(rn.x)), rho * r0.z) : kInf;

@@ -37,6 +37,9 @@ struct SampTab {
 struct DevTables {
   int n_mat, n_e;
   float lnE_lo, inv_dlnE;
+  float x_lg2, x_lo;  // grid position = log2(E) * x_lg2 + x_lo
+  // per-material tables [n_mat][n_e][2]: the node's value, then its
+  // difference to the next node (zero at the last node)
   const float4 *ph;    // {mu/rho total (cm^2/g), Compton fraction, photoelectric fraction, 0}
   const float4 *el;    // {R (g/cm^2), S (MeV cm^2/g), Sigma_hard (cm^2/g), 1/lambda1 (cm^2/g)}
   const float *pmol;   // Moller fraction of Sigma_hard

@@ -143,7 +143,14 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-// Lane-level sink: tally with run-length coalescing, counters, and queue pushes.
+// Lane-level sink: tally with run-length coalescing, counters, and queue
+// pushes.  kMulti: a batch launch, whose particles carry their job index.
+// kCount: also count events (steps, flights, interactions, tally atomics,
+// pushes) for the run statistics; the energy counters (emitted, escaped,
+// missed) are always kept.  The event counts live in registers across the
+// whole loop and cost about 10 % of the transport rate, so runs count them
+// only on request (dpm_run_opts.count_events).
+template <bool kMulti, bool kCount>
 struct QSink {
   const RunParams &R;
   const QDev &Q;
@@ -164,7 +171,7 @@ struct QSink {
   __device__ __forceinline__ void flush() {
     if (pend_v >= 0 && pend_q != 0) {
       atomicAdd(slab + pend_v, (unsigned long long)pend_q);
-      ++cnt[C_ATOM];
+      if (kCount) ++cnt[C_ATOM];
     }
     pend_v = -1;
     pend_q = 0;
@@ -181,15 +188,21 @@ struct QSink {
   }
   __device__ __forceinline__ void escape(float E) { cnt[C_ESC] += fxc(E); }
   __device__ __forceinline__ void error(int e) { err |= e; }
-  __device__ __forceinline__ void count_step() { ++cnt[C_ESTEP]; }
-  __device__ __forceinline__ void count_flight() { ++cnt[C_GFLIGHT]; }
-  __device__ __forceinline__ void count_interaction() { ++cnt[C_GINT]; }
+  __device__ __forceinline__ void count_step() {
+    if (kCount) ++cnt[C_ESTEP];
+  }
+  __device__ __forceinline__ void count_flight() {
+    if (kCount) ++cnt[C_GFLIGHT];
+  }
+  __device__ __forceinline__ void count_interaction() {
+    if (kCount) ++cnt[C_GINT];
+  }
 
   // Warp-aggregated push of the lanes that are here together: one atomic on
   // the shard's tail per queue type, then each lane writes its record and
   // publishes its slot.
   __device__ DPM_COLD void push(const Part &q) {
-    ++cnt[C_PUSH];
+    if (kCount) ++cnt[C_PUSH];
     const int t = (q.type == PHOTON) ? 0 : 1;
     const unsigned act = __activemask();
     const unsigned mt = __ballot_sync(act, t == 1);
@@ -253,7 +266,7 @@ struct QSink {
     Qt.idl[idx] = q.id_lo;
     Qt.idh[idx] = q.id_hi;
     Qt.hist[idx] = q.hist | (q.type == POSITRON ? 0x80000000u : 0u);
-    Qt.job[idx] = uint32_t(q.job);
+    if (kMulti) Qt.job[idx] = uint32_t(q.job);
     st_release32(Qt.seq + idx, uint32_t(p + 1));
   }
 };
@@ -283,6 +296,7 @@ __device__ __forceinline__ int claim(const QType &Qt, int s, int want, unsigned 
 
 // Read the record at position p of shard s (waiting for its publication) and
 // free the slot for the producer one lap later.
+template <bool kMulti>
 __device__ __forceinline__ bool take(const QDev &Q, int t, int s, unsigned long long p, Part &o, int &err) {
   const QType &Qt = Q.q[t];
   const uint32_t slot = uint32_t(p) & Q.mask;
@@ -313,7 +327,7 @@ __device__ __forceinline__ bool take(const QDev &Q, int t, int s, unsigned long 
   const uint32_t h = __ldcg(Qt.hist + idx);
   o.hist = h & 0x7fffffffu;
   o.type = t == 0 ? PHOTON : ((h >> 31) ? POSITRON : ELECTRON);
-  o.job = int(__ldcg(Qt.job + idx));
+  o.job = kMulti ? int(__ldcg(Qt.job + idx)) : 0;
   o.ctr = 0;
   st_release32(Qt.seq + idx, uint32_t(p + (1ull << Q.log2cs)));
   return true;
@@ -321,6 +335,7 @@ __device__ __forceinline__ bool take(const QDev &Q, int t, int s, unsigned long 
 
 // Fill the warp's empty lanes from queue t (home shard first, then a few
 // others).  Returns the number of lanes filled (warp-uniform).
+template <bool kMulti>
 __device__ int refill_queue(const QDev &Q, int t, int home, int probes, unsigned empty, Part &p, bool &alive,
                             int &err) {
   const int want = __popc(empty);
@@ -337,7 +352,7 @@ __device__ int refill_queue(const QDev &Q, int t, int home, int probes, unsigned
   if (lane == 0) atomicAdd(&Q.backlog[t].v, (unsigned long long)(-(long long)n));
   if (empty & (1u << lane)) {
     const int rank = __popc(empty & lanemask_lt());
-    if (rank < n) alive = take(Q, t, s, base + rank, p, err);
+    if (rank < n) alive = take<kMulti>(Q, t, s, base + rank, p, err);
   }
   return n;
 }
@@ -352,9 +367,9 @@ __device__ __forceinline__ JobCtx job_ctx(const RunParams &R, int j) {
 // (batch) from the current job of the batch, job after job, so that one
 // job's phantom and tally are hot in L2 at a time.  A warp holding particles
 // of one type only starts histories of a job with that beam type.
-template <bool kMulti>
-__device__ int refill_source(const RunParams &R, const QDev &Q, unsigned empty, Part &p, bool &alive, QSink &sk,
-                             int &type) {
+template <bool kMulti, bool kCount>
+__device__ int refill_source(const RunParams &R, const QDev &Q, unsigned empty, Part &p, bool &alive,
+                             QSink<kMulti, kCount> &sk, int &type) {
   const int want = __popc(empty);
   if (want == 0) return 0;
   const int lane = threadIdx.x & 31;
@@ -396,8 +411,8 @@ __device__ int refill_source(const RunParams &R, const QDev &Q, unsigned empty, 
       } else {
         hit = make_primary(p, R, uint32_t(hl));
       }
-      sk.cnt[C_EMIT] += QSink::fxc(p.E);
-      if (!hit) sk.cnt[C_MISS] += QSink::fxc(p.E);
+      sk.cnt[C_EMIT] += QSink<kMulti, kCount>::fxc(p.E);
+      if (!hit) sk.cnt[C_MISS] += QSink<kMulti, kCount>::fxc(p.E);
       alive = hit;
     }
   }
@@ -501,7 +516,7 @@ __device__ void reduce_counters_q(const long long *cnt, int err, const RunParams
 #ifndef DPM_QUEUE_MIN_BLOCKS
 #define DPM_QUEUE_MIN_BLOCKS 8
 #endif
-template <bool kMulti>
+template <bool kMulti, bool kCount>
 __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
     k_queue(const __grid_constant__ RunParams R, const __grid_constant__ QDev Q) {
   const int lane = threadIdx.x & 31;
@@ -509,7 +524,7 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
   const int src_type = (R.S.particle == 0) ? 0 : 1;
   const size_t V = size_t(R.P.nx) * R.P.ny * R.P.nz;
   if (lane == 0) atomicAdd(&Q.started->v, 1ull);
-  QSink sk(R, Q, home);
+  QSink<kMulti, kCount> sk(R, Q, home);
   Part p{};
   bool alive = false;
   int nstep = 0;
@@ -536,24 +551,24 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
       const int ph = grid_phase(Q, S, R.counters);
       if (mode < 0) {
         if (ph == 1) {
-          if (refill_queue(Q, O, home, 0, empty, p, alive, sk.err)) mode = O;
-          else if (refill_queue(Q, O, home, kStealProbes, empty, p, alive, sk.err)) mode = O;
-          else if (refill_queue(Q, S, home, 0, empty, p, alive, sk.err)) mode = S;
-          else if (refill_queue(Q, S, home, kStealProbes, empty, p, alive, sk.err)) mode = S;
+          if (refill_queue<kMulti>(Q, O, home, 0, empty, p, alive, sk.err)) mode = O;
+          else if (refill_queue<kMulti>(Q, O, home, kStealProbes, empty, p, alive, sk.err)) mode = O;
+          else if (refill_queue<kMulti>(Q, S, home, 0, empty, p, alive, sk.err)) mode = S;
+          else if (refill_queue<kMulti>(Q, S, home, kStealProbes, empty, p, alive, sk.err)) mode = S;
         } else {
           int ty = S;
-          if (refill_queue(Q, S, home, 0, empty, p, alive, sk.err)) mode = S;
-          else if (source_allowed(Q, home, Q.guard[S]) && refill_source<kMulti>(R, Q, empty, p, alive, sk, ty)) mode = S;
-          else if (refill_queue(Q, O, home, 0, empty, p, alive, sk.err)) mode = O;
-          else if (refill_queue(Q, O, home, kStealProbes, empty, p, alive, sk.err)) mode = O;
-          else if (refill_queue(Q, S, home, kStealProbes, empty, p, alive, sk.err)) mode = S;
+          if (refill_queue<kMulti>(Q, S, home, 0, empty, p, alive, sk.err)) mode = S;
+          else if (source_allowed(Q, home, Q.guard[S]) && refill_source<kMulti, kCount>(R, Q, empty, p, alive, sk, ty)) mode = S;
+          else if (refill_queue<kMulti>(Q, O, home, 0, empty, p, alive, sk.err)) mode = O;
+          else if (refill_queue<kMulti>(Q, O, home, kStealProbes, empty, p, alive, sk.err)) mode = O;
+          else if (refill_queue<kMulti>(Q, S, home, kStealProbes, empty, p, alive, sk.err)) mode = S;
         }
       } else if (mode == S) {
         int ty = S;
-        if (ph == 0 && !refill_queue(Q, S, home, 0, empty, p, alive, sk.err) && source_allowed(Q, home, Q.guard[S]))
-          refill_source<kMulti>(R, Q, empty, p, alive, sk, ty);
+        if (ph == 0 && !refill_queue<kMulti>(Q, S, home, 0, empty, p, alive, sk.err) && source_allowed(Q, home, Q.guard[S]))
+          refill_source<kMulti, kCount>(R, Q, empty, p, alive, sk, ty);
       } else if (ph == 1 || source_exhausted<kMulti>(R, Q)) {
-        refill_queue(Q, O, home, kStealProbes, empty, p, alive, sk.err);
+        refill_queue<kMulti>(Q, O, home, kStealProbes, empty, p, alive, sk.err);
       }
       if (alive && !was_alive) {
         if (kMulti) {
@@ -640,25 +655,33 @@ __global__ void k_queue_init(uint32_t *seq0, uint32_t *seq1, size_t n, uint32_t 
 
 }  // namespace
 
+// The queue kernel's instantiations: batch launch (kMulti) x event counts.
+using QKernel = void (*)(RunParams, QDev);
+const QKernel kQueueKernels[4] = {k_queue<false, false>, k_queue<false, true>, k_queue<true, false>,
+                                  k_queue<true, true>};
+
 int queue_blocks_per_sm() {
   // the kernel keeps no shared memory: give the whole carveout to L1, where
   // the tables are cached
-  cudaFuncSetAttribute(k_queue<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-  cudaFuncSetAttribute(k_queue<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-  int per_sm = 0, per_sm_multi = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_queue<false>, kQBlock, 0) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_multi, k_queue<true>, kQBlock, 0) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
+  int best = 1 << 30;
+  for (QKernel k : kQueueKernels) {
+    int per_sm = 0;
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kQBlock, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    best = std::min(best, per_sm);
   }
-  return std::min(per_sm, per_sm_multi);
+  return best;
 }
 
 int queue_preload() {
   // cudaFuncGetAttributes loads a kernel under lazy module loading
   cudaFuncAttributes a;
-  if (cudaFuncGetAttributes(&a, k_queue<false>) != cudaSuccess || cudaFuncGetAttributes(&a, k_queue<true>) != cudaSuccess ||
-      cudaFuncGetAttributes(&a, k_queue_init) != cudaSuccess) {
+  bool ok = cudaFuncGetAttributes(&a, k_queue_init) == cudaSuccess;
+  for (QKernel k : kQueueKernels) ok = ok && cudaFuncGetAttributes(&a, k) == cudaSuccess;
+  if (!ok) {
     cudaGetLastError();
     return 0;
   }
@@ -733,8 +756,14 @@ int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batc
   }
   k_queue_init<<<sm_count * 4, 256, 0, st>>>(Q.q[0].seq, Q.q[1].seq, slots, Q.mask);
   if (start) cudaEventRecord(start, st);
-  if (R.jobs) k_queue<true><<<K, kQBlock, 0, st>>>(R, Q);
-  else k_queue<false><<<K, kQBlock, 0, st>>>(R, Q);
+  const bool count = o.count_events != 0;
+  if (R.jobs) {
+    if (count) k_queue<true, true><<<K, kQBlock, 0, st>>>(R, Q);
+    else k_queue<true, false><<<K, kQBlock, 0, st>>>(R, Q);
+  } else {
+    if (count) k_queue<false, true><<<K, kQBlock, 0, st>>>(R, Q);
+    else k_queue<false, false><<<K, kQBlock, 0, st>>>(R, Q);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = cudaGetErrorString(e);

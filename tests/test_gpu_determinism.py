@@ -149,3 +149,29 @@ def test_clone_phantom_equals_a_fresh_load():
     assert st["n_histories"] == 200000 and src_st["n_histories"] == 100000
     assert np.array_equal(got, ref)
     assert not np.array_equal(src_raw, ref)
+
+
+@pytest.mark.parametrize("make,n", [(W.c1_photon_wbw, 200_000), (W.c0_electron_wlw, 4000)], ids=["6mv", "e20"])
+def test_event_counting_changes_nothing_but_the_counts(make, n):
+    """The queue kernel with and without event counts gives the same tally and
+    energy counters; its counts equal the per-history kernel's (the same
+    particles take the same steps), and without counting they read zero."""
+    wl = make()
+
+    def run(kernel, count):
+        with dpm.Dpm(0, W.MATERIALS, wl.params) as d:
+            pid = d.load_phantom(wl.phantom)
+            d.run(pid, wl.source, n, wl.seed, kernel=kernel, count_events=count)
+            _, _, raw, st = d.read(pid)
+        assert st["error_flags"] == 0
+        return raw, st
+
+    raw0, st0 = run(dpm.KERNEL_QUEUE, 0)
+    raw1, st1 = run(dpm.KERNEL_QUEUE, 1)
+    rawh, sth = run(dpm.KERNEL_HISTORY, 0)
+    assert np.array_equal(raw0, raw1) and np.array_equal(raw0, rawh)
+    for k in ("emitted", "escaped", "missed", "n_histories"):
+        assert st0[k] == st1[k] == sth[k], k
+    for k in ("n_e_steps", "n_g_flights", "n_g_interactions", "n_pushed"):
+        assert st1[k] == sth[k] > 0 and st0[k] == 0, k
+    assert st1["n_tally_atomics"] > 0 and st0["n_tally_atomics"] == 0

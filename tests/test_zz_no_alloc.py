@@ -38,7 +38,7 @@ def test_noalloc_matches_dpm_run_on_two_calls(gpu_lib, make, n):
         st1 = dpm.dpm_run_noalloc(d.ctx, pid, wl.source, 0, n, wl.seed, tally.data_ptr())
         assert _free_bytes(torch) == f0
         got1 = tally.cpu().numpy().copy()
-        d.run(pid, wl.source, n, wl.seed, first=0, kernel=dpm.KERNEL_QUEUE)
+        d.run(pid, wl.source, n, wl.seed, first=0, kernel=dpm.KERNEL_QUEUE, count_events=1)
         ref1 = d.read(pid)
         assert got1.sum() > 0
         assert np.array_equal(got1, ref1[2])
