@@ -367,9 +367,10 @@ def main():
     dose, sigma, raw, st = d.read(pid)
     n_tot = n * args.steps
     value = world * n_tot / (tot_ms / 1000.0)
-    # event counts (tally atomics, secondaries) for the roofline: one more
-    # step with counting on, after the timed region (the timed steps do not
-    # count events, see dpm_run_opts.count_events); same histories, same tally
+    # run counters (tally atomics and secondaries for the roofline, energies
+    # for the balance): one more step with counting on, after the timed region
+    # (the timed steps do not count, see dpm_run_opts.count_events); same
+    # histories, same tally
     d.reset(pid)
     d.run(pid, wl.source, n, wl.seed, first=sharding.history_range(rank, world, 0, n)[0], kernel=kernel,
           count_events=1)
@@ -413,7 +414,8 @@ def main():
             "mean_sigma_rel_above_half_dmax": mean_rel_50,
             "clocks": clk, "gpu_launches": launches_per_step * args.steps,
             "wall_s_timed_region": wall,
-            "energy_balance_rel": abs(st["emitted"] - st["deposited"] - st["escaped"] - st["missed"]) / st["emitted"]}
+            "energy_balance_rel": abs(st_cnt["emitted"] - st_cnt["deposited"] - st_cnt["escaped"] - st_cnt["missed"])
+            / st_cnt["emitted"]}
 
     # L2 roofline: the tally's scattered 64-bit atomics and the L1->L2 sector
     # traffic (per history, from the committed ncu capture) against this GPU's

@@ -44,7 +44,7 @@ def test_batch_equals_jobs_run_alone(reference, use_graph):
     with dpm.Dpm(0, W.MATERIALS, PARAMS) as d:
         pids = [d.load_phantom(j[0]) for j in spec]
         jobs = [(pid, src, first, n, seed) for pid, (_, src, first, n, seed) in zip(pids, spec)]
-        dpm.dpm_run_batch(d.ctx, jobs, dpm.run_opts(use_graph=use_graph))
+        dpm.dpm_run_batch(d.ctx, jobs, dpm.run_opts(use_graph=use_graph, count_events=1))
         st = dpm.dpm_batch_stats(d.ctx)
         raws = [d.read(pid)[2] for pid in pids]
     assert st["error_flags"] == 0 and st["n_histories"] == sum(j[3] for j in spec)

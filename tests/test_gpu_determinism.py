@@ -170,7 +170,7 @@ def test_event_counting_changes_nothing_but_the_counts(make, n):
     raw1, st1 = run(dpm.KERNEL_QUEUE, 1)
     rawh, sth = run(dpm.KERNEL_HISTORY, 0)
     assert np.array_equal(raw0, raw1) and np.array_equal(raw0, rawh)
-    for k in ("emitted", "escaped", "missed", "n_histories"):
+    for k in ("emitted", "escaped", "missed", "deposited", "n_histories"):
         assert st0[k] == st1[k] == sth[k], k
     for k in ("n_e_steps", "n_g_flights", "n_g_interactions", "n_pushed"):
         assert st1[k] == sth[k] > 0 and st0[k] == 0, k

@@ -74,7 +74,8 @@ def oracle_result(name):
 def gpu_run(wl, n, kernel, seed=None, params=None, n_batches=50, first=0):
     with dpm.Dpm(0, W.MATERIALS, params or wl.params) as d:
         pid = d.load_phantom(wl.phantom)
-        d.run(pid, wl.source, n, wl.seed if seed is None else seed, first=first, kernel=kernel, n_batches=n_batches)
+        d.run(pid, wl.source, n, wl.seed if seed is None else seed, first=first, kernel=kernel, n_batches=n_batches,
+              count_events=1)
         return d.read(pid)
 
 
@@ -159,7 +160,7 @@ def test_missed_beam_and_empty_run(kernel):
         d.run(pid, src, 0, 1, kernel=kernel)
         _, _, raw0, st0 = d.read(pid)
         assert raw0.sum() == 0 and st0["n_histories"] == 0
-        d.run(pid, src, 5000, 1, kernel=kernel)
+        d.run(pid, src, 5000, 1, kernel=kernel, count_events=1)
         dose, sigma, raw, st = d.read(pid)
     assert raw.sum() == 0 and dose.sum() == 0
     assert st["missed"] == pytest.approx(st["emitted"], rel=1e-9)
@@ -208,7 +209,7 @@ def test_straight_track_across_the_largest_index_range(kernel, axis):
     orc = O.run(ph, W.MATERIALS, W.DEFAULT_PARAMS, src, 1, 1, workers=1, flags=O.OR_NO_HARD | O.OR_NO_MSC)
     with dpm.Dpm(0, W.MATERIALS, W.DEFAULT_PARAMS) as d_:
         pid = d_.load_phantom(ph)
-        d_.run(pid, src, 64, 1, kernel=kernel, physics_flags=dpm.NO_HARD | dpm.NO_MSC)
+        d_.run(pid, src, 64, 1, kernel=kernel, physics_flags=dpm.NO_HARD | dpm.NO_MSC, count_events=1)
         _, _, raw, st = d_.read(pid)
     got = raw / 2.0 ** 32 / 64
     ref = orc.S1
