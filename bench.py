@@ -532,6 +532,19 @@ def bench_batch(args, rank, world, local):
         torch.cuda.synchronize()
         plain.append(a.elapsed_time(b))
     plain_ms = min(plain)
+    # ceiling of any launch arrangement: every job at the rate it reaches in
+    # a long run of its own (at least 4e6 histories, where the launch's
+    # start-up and tail are a few % of it); the jobs' histories at those rates
+    ideal_ms = 0.0
+    for k, (pid, src, first, n, seed) in enumerate(jobs_for(3000)):
+        m = max(n, 4_000_000)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dpm.dpm_run(d.ctx, pid, src, 10 ** 9 + first, m, seed, dpm.run_opts(n_batches=10, **opts))
+        b.record(stream)
+        torch.cuda.synchronize()
+        ideal_ms += a.elapsed_time(b) * n / m
     d.close()
     value = world * n_step / (batch_ms / 1000.0)
     line = {"metric": "histories/s", "value": value, "unit": "histories/s", "n_gpus": world, "steps": args.steps,
@@ -544,6 +557,9 @@ def bench_batch(args, rank, world, local):
             "single_run_path": {"ms_per_step": plain_ms, "value": world * n_step / (plain_ms / 1000.0),
                                 "what": "the same 64 jobs as 64 dpm_run calls"},
             "speedup_vs_single_runs": plain_ms / batch_ms,
+            "steady_state_ceiling": {"ms_per_step": ideal_ms, "speedup_vs_single_runs": plain_ms / ideal_ms,
+                                     "what": "each job at the rate of a long run of its own (>= 4e6 histories): "
+                                             "the gain any arrangement of the launches could reach"},
             "batch_error_flags": st["error_flags"],
             "clocks": clk, "gpu_launches": args.steps * (2 + len(spec))}
     if rank == 0:

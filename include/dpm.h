@@ -92,7 +92,13 @@ typedef struct {
 } dpm_source;
 
 /* Kernel selection and launch shape.  Zero fields take defaults. */
-enum { DPM_KERNEL_QUEUE = 0, DPM_KERNEL_HISTORY = 1, DPM_KERNEL_PAPER_F32 = 2, DPM_KERNEL_PAPER_CAS = 3 };
+enum {
+    DPM_KERNEL_QUEUE = 0,
+    DPM_KERNEL_HISTORY = 1,
+    DPM_KERNEL_PAPER_F32 = 2,
+    DPM_KERNEL_PAPER_CAS = 3,
+    DPM_KERNEL_HISTORY_F64 = 4
+};
 typedef struct {
     int kernel;        /* DPM_KERNEL_QUEUE (persistent, particle queues);
                           DPM_KERNEL_HISTORY (one history per thread, private stack);
@@ -103,7 +109,13 @@ typedef struct {
                           a compare-and-swap loop), then rounded to the fixed-point tally.
                           Same trajectories as the other kernels; the tally differs from
                           theirs by float rounding and is not reproducible bit for bit.
-                          dpm_run only (DPM_EINVAL elsewhere or for other values). */
+                          DPM_KERNEL_HISTORY_F64: DPM_KERNEL_HISTORY with every transport
+                          operation in FP64 and the tables in FP64 (Sec. 2.3 runs the
+                          transport in single precision; this measures what that costs).
+                          Same random numbers; trajectories part from the FP32 ones where
+                          a rounding flips a decision, so its tally agrees statistically.
+                          The kernels other than DPM_KERNEL_QUEUE are dpm_run only
+                          (DPM_EINVAL elsewhere or for other values). */
     int n_batches;     /* history batches for the sigma estimate (default 50, max 1024) */
     int block_size;    /* per-history kernel: threads per block (multiple of 32; 0 = 128).
                           The queue kernel always runs blocks of 128 threads (it schedules
@@ -114,7 +126,10 @@ typedef struct {
                           photon warps, 12 for electron warps) */
     double timeout_s;  /* bound on any device wait (default 20 s) */
     int physics_flags; /* DPM_NO_HARD: no Moller/bremsstrahlung events; DPM_NO_MSC: no
-                          elastic deflections (test and ablation switches; 0 = full physics) */
+                          elastic deflections (test and ablation switches; 0 = full physics);
+                          DPM_SAUTER: photoelectrons leave at Sauter's K-shell polar angle
+                          about the photon direction (default: along it); dpm_run only
+                          (dpm_run_batch returns DPM_EINVAL) */
     int queue_limit;   /* fault injection: largest occupancy of a queue shard (0 = capacity);
                           a push that finds no shard below it is an overflow */
     int use_graph;     /* dpm_run_batch only: capture zero -> transport -> fold in a CUDA
@@ -125,7 +140,7 @@ typedef struct {
                           counters and the tally are the same either way.  The per-history
                           kernels always count. */
 } dpm_run_opts;
-enum { DPM_NO_HARD = 1, DPM_NO_MSC = 2 };
+enum { DPM_NO_HARD = 1, DPM_NO_MSC = 2, DPM_SAUTER = 4 };
 
 /* Run summary returned by dpm_read_dose(). Energies in MeV. */
 typedef struct {
@@ -362,7 +377,8 @@ int dpm_diag_table(dpm_ctx *ctx, int which, int mat, int n, const double *energy
    6 exponential path -ln(u) in mean free paths, 7 direction rotation: the
    unit vector (0.36, -0.48, 0.8) (aux 0..2) or +z (aux 3..5) turned by polar
    cosine e and azimuth 2 pi u, its component int(aux) % 3, 8 path from
-   x = u cm to the far face of a 1 cm voxel [0, 1) along direction cosine e. */
+   x = u cm to the far face of a 1 cm voxel [0, 1) along direction cosine e,
+   9 Sauter's 1 - cos(theta) of a photoelectron of kinetic energy e. */
 int dpm_diag_sample(dpm_ctx *ctx, int which, double e, double aux, int n, const double *u, double *out);
 
 /* n Philox4x32-10 blocks for counters ctr[4*i..] and keys key[2*i..] (host). */

@@ -548,6 +548,26 @@ static double sample_msc(double A, ranecu *r) {
     return 2.0 * A * x / (1.0 + A - x);
 }
 
+/* Photoelectron direction (the DPM physics of Sec. 2.1 gives the K-shell
+   photoelectron Sauter's angular distribution; optional here, OR_SAUTER):
+   dsigma/dOmega ~ sin^2(th)/(1 - b cos th)^4 [1 + g(g-1)(g-2)(1 - b cos th)/2]
+   with b, g the electron's speed and Lorentz factor.  In nu = 1 - cos th,
+   with A = 1/b - 1 and B = b g(g-1)(g-2)/2, the density is
+   p(nu) ~ nu(2 - nu) [1/(A+nu)^4 + B/(A+nu)^3] on [0, 2].  Propose
+   q(nu) ~ nu/(A+nu)^3, whose CDF is (x/x_max)^2 in x = nu/(A+nu)
+   (x_max = 2/(A+2)), and accept with (2 - nu)((1-x)/A + B) over its bound
+   2(1/A + max(B, 0)).  Returns nu. */
+static double sample_sauter(double T, ranecu *r) {
+    double g = 1.0 + T / MC2, b = sqrt(T * (T + 2.0 * MC2)) / (T + MC2);
+    double A = 1.0 / b - 1.0, B = 0.5 * b * g * (g - 1.0) * (g - 2.0);
+    double xm = 2.0 / (A + 2.0), M = 2.0 * (1.0 / A + (B > 0 ? B : 0.0));
+    for (;;) {
+        double x = xm * sqrt(ranecu_next(r));
+        double nu = A * x / (1.0 - x);
+        if (ranecu_next(r) * M <= (2.0 - nu) * ((1.0 - x) / A + B)) return nu;
+    }
+}
+
 /* 6 MV energy by bisection on the CDF. */
 static double sample_spectrum(ranecu *r) {
     double u = ranecu_next(r);
@@ -574,6 +594,7 @@ void or_sample(int which, double a, double b, const or_material *m, uint64_t n, 
             case OR_S_PAIR: out[i] = sample_pair(a, &r); break;
             case OR_S_MSC: out[i] = sample_msc(a, &r); break;
             case OR_S_SPECTRUM: out[i] = sample_spectrum(&r); break;
+            case OR_S_SAUTER: out[i] = sample_sauter(a, &r); break;
             default: out[i] = 0;
         }
     }
@@ -768,9 +789,14 @@ static int transport_photon(tctx *c, part *p, int first_flight_only) {
             p->E = Ep;
             continue;
         } else if (r < muc[m] + mup[m]) {
-            /* photoelectric: the electron takes all the energy, same direction */
+            /* photoelectric: the electron takes all the energy, along the
+               photon direction or (OR_SAUTER) at Sauter's polar angle */
             part el = *p;
             el.type = 1;
+            if ((c->p->flags & OR_SAUTER) && el.E > c->p->eabs_e) {
+                double nu = sample_sauter(el.E, &c->rng);
+                rotate(el.d, 1.0 - nu, 2.0 * PI * ranecu_next(&c->rng));
+            }
             emit_charged(c, &el);
             return 0;
         } else {
@@ -961,8 +987,20 @@ static void tctx_free(tctx *c) {
 
 int or_run(const or_phantom *ph, const or_material *mats, int n_mat, const or_params *p, const or_source *src,
            uint64_t h_begin, uint64_t h_end, uint64_t seed, double *S1, double *S2, or_stats *st) {
+    return or_run_planes(ph, mats, n_mat, p, src, h_begin, h_end, seed, S1, S2, NULL, st);
+}
+
+/* or_run, plus (if P2 is not NULL) the history-by-history second moment of
+   the energy deposited in each z plane: P2[k] += (sum over the plane's voxels
+   of the history's deposits)^2, for the exact variance of depth-dose
+   integrals (Sec. 3's sigma_D, applied to a plane instead of a voxel). */
+int or_run_planes(const or_phantom *ph, const or_material *mats, int n_mat, const or_params *p,
+                  const or_source *src, uint64_t h_begin, uint64_t h_end, uint64_t seed, double *S1, double *S2,
+                  double *P2, or_stats *st) {
     if (n_mat > OR_MAXMAT) return -1;
     memset(st, 0, sizeof(*st));
+    const long nxy = (long)ph->nx * ph->ny;
+    double *plane = P2 ? (double *)calloc((size_t)ph->nz, sizeof(double)) : NULL;
     tctx *c = (tctx *)malloc(sizeof(tctx));
     tctx_init(c, ph, mats, n_mat, p, st);
     for (uint64_t h = h_begin; h < h_end; h++) {
@@ -991,7 +1029,17 @@ int or_run(const or_phantom *ph, const or_material *mats, int n_mat, const or_pa
             double e = c->hE[v];
             S1[v] += e;
             S2[v] += e * e;
+            if (plane) plane[v / nxy] += e;
             c->hE[v] = 0.0;
+        }
+        if (plane) {
+            for (long i = 0; i < c->n_touched; i++) {
+                long k = c->touched[i] / nxy;
+                if (plane[k] != 0.0) {
+                    P2[k] += plane[k] * plane[k];
+                    plane[k] = 0.0;
+                }
+            }
         }
         c->n_touched = 0;
         st->deposited += c->h_dep;
@@ -1003,6 +1051,7 @@ int or_run(const or_phantom *ph, const or_material *mats, int n_mat, const or_pa
     int err = c->err;
     tctx_free(c);
     free(c);
+    free(plane);
     return err ? -2 : 0;
 }
 

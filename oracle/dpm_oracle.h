@@ -41,7 +41,7 @@ typedef struct {
     double rho_de;  /* density (g/cm^3) of the density-effect correction; 0: none */
 } or_material;
 
-enum { OR_NO_HARD = 1, OR_NO_MSC = 2, OR_NO_SECONDARY_PHOTONS = 4 };
+enum { OR_NO_HARD = 1, OR_NO_MSC = 2, OR_NO_SECONDARY_PHOTONS = 4, OR_SAUTER = 8 };
 
 typedef struct {
     double eabs_e, eabs_g, wcc, wcr, f_e, c_pe;
@@ -78,6 +78,11 @@ typedef struct {
 int or_run(const or_phantom *ph, const or_material *mats, int n_mat, const or_params *p,
            const or_source *src, uint64_t h_begin, uint64_t h_end, uint64_t seed,
            double *S1, double *S2, or_stats *st);
+/* or_run plus, if P2 is not NULL (nz doubles, accumulated), the sum over
+   histories of the squared energy each history deposits in each z plane. */
+int or_run_planes(const or_phantom *ph, const or_material *mats, int n_mat, const or_params *p,
+                  const or_source *src, uint64_t h_begin, uint64_t h_end, uint64_t seed, double *S1, double *S2,
+                  double *P2, or_stats *st);
 
 /* Primary photons only: counts those leaving the phantom without any
    interaction (narrow-beam uncollided transmission). */
@@ -114,7 +119,7 @@ double or_spectrum_cdf(double E);
 
 /* samplers (n draws into out[], RANECU seeded from seed) ------------------ */
 void or_sample(int which, double a, double b, const or_material *m, uint64_t n, uint64_t seed, double *out);
-enum { OR_S_KN = 0, OR_S_MOLLER = 1, OR_S_BREMS = 2, OR_S_PAIR = 3, OR_S_MSC = 4, OR_S_SPECTRUM = 5 };
+enum { OR_S_KN = 0, OR_S_MOLLER = 1, OR_S_BREMS = 2, OR_S_PAIR = 3, OR_S_MSC = 4, OR_S_SPECTRUM = 5, OR_S_SAUTER = 6 };
 
 /* RANECU stream for pins: n uniforms from (s1, s2) */
 void or_ranecu_stream(int32_t s1, int32_t s2, int n, double *out, int32_t *state_out);

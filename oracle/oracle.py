@@ -24,8 +24,8 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _SOURCES = [os.path.join(_HERE, "dpm_oracle.c")]
 
-OR_NO_HARD, OR_NO_MSC, OR_NO_SECONDARY_PHOTONS = 1, 2, 4
-S_KN, S_MOLLER, S_BREMS, S_PAIR, S_MSC, S_SPECTRUM = range(6)
+OR_NO_HARD, OR_NO_MSC, OR_NO_SECONDARY_PHOTONS, OR_SAUTER = 1, 2, 4, 8
+S_KN, S_MOLLER, S_BREMS, S_PAIR, S_MSC, S_SPECTRUM, S_SAUTER = range(7)
 
 
 def build(force: bool = False) -> str:
@@ -99,6 +99,9 @@ def lib():
         L.or_run.argtypes = [C.POINTER(PhantomS), pm, i, C.POINTER(Params), C.POINTER(SourceS), u64, u64, u64, pd, pd,
                              C.POINTER(Stats)]
         L.or_run.restype = i
+        L.or_run_planes.argtypes = [C.POINTER(PhantomS), pm, i, C.POINTER(Params), C.POINTER(SourceS), u64, u64, u64,
+                                    pd, pd, pd, C.POINTER(Stats)]
+        L.or_run_planes.restype = i
         L.or_uncollided.argtypes = [C.POINTER(PhantomS), pm, i, C.POINTER(Params), C.POINTER(SourceS), u64, u64]
         L.or_uncollided.restype = C.c_longlong
         _lib = L
@@ -153,6 +156,15 @@ class OracleResult:
     S2: np.ndarray      # sum over histories of its square, MeV^2
     n: int
     stats: dict
+    P2: np.ndarray = None  # per z plane: sum over histories of the plane's energy squared (planes=True)
+
+    def plane_energy_and_sigma(self, nz):
+        """Mean energy per history deposited in each z plane and its standard
+        error, history by history (run with planes=True)."""
+        n = self.n
+        e = self.S1.reshape(nz, -1).sum(axis=1) / n
+        var = np.maximum(self.P2 / n - e * e, 0.0)
+        return e, np.sqrt(var / max(n - 1, 1))
 
     def mean_energy(self):
         return self.S1 / self.n
@@ -173,49 +185,56 @@ class OracleResult:
 
 
 def _run_chunk(args):
-    ph, mats_d, pd, src, h0, h1, seed, flags = args
+    ph, mats_d, pd, src, h0, h1, seed, flags, planes = args
     keep = []
     phs = phantom_struct(ph, keep)
     V = ph.n_vox
     S1 = np.zeros(V, np.float64)
     S2 = np.zeros(V, np.float64)
+    P2 = np.zeros(ph.nz, np.float64) if planes else None
     st = Stats()
     mats = materials(mats_d)
-    rc = lib().or_run(C.byref(phs), mats, len(mats_d), C.byref(params(pd, flags)), C.byref(source(src)), h0, h1,
-                      seed, S1.ctypes.data_as(C.POINTER(C.c_double)), S2.ctypes.data_as(C.POINTER(C.c_double)),
-                      C.byref(st))
+    dp = C.POINTER(C.c_double)
+    rc = lib().or_run_planes(C.byref(phs), mats, len(mats_d), C.byref(params(pd, flags)), C.byref(source(src)),
+                             h0, h1, seed, S1.ctypes.data_as(dp), S2.ctypes.data_as(dp),
+                             P2.ctypes.data_as(dp) if planes else None, C.byref(st))
     if rc != 0:
         raise RuntimeError(f"oracle run failed with {rc}")
-    return S1, S2, st.as_dict()
+    return S1, S2, P2, st.as_dict()
 
 
-def run(ph, mats_d, pd, src, n, seed, h0=0, workers=None, flags=0, chunks_per_worker=4) -> OracleResult:
-    """Transport histories [h0, h0+n) and return the per-voxel sums."""
+def run(ph, mats_d, pd, src, n, seed, h0=0, workers=None, flags=0, chunks_per_worker=4,
+        planes=False) -> OracleResult:
+    """Transport histories [h0, h0+n) and return the per-voxel sums (and,
+    with planes=True, the per-z-plane second moments)."""
     if workers is None:
         workers = os.cpu_count() or 1
     workers = max(1, min(workers, n if n > 0 else 1))
     if workers == 1 or n < 64:
-        S1, S2, st = _run_chunk((ph, mats_d, pd, src, h0, h0 + n, seed, flags))
-        return OracleResult(S1, S2, n, st)
+        S1, S2, P2, st = _run_chunk((ph, mats_d, pd, src, h0, h0 + n, seed, flags, planes))
+        return OracleResult(S1, S2, n, st, P2)
     import multiprocessing as mp
     k = workers * chunks_per_worker
     edges = [h0 + (n * i) // k for i in range(k + 1)]
-    jobs = [(ph, mats_d, pd, src, edges[i], edges[i + 1], seed, flags) for i in range(k)]
+    jobs = [(ph, mats_d, pd, src, edges[i], edges[i + 1], seed, flags, planes) for i in range(k)]
     ctx = mp.get_context("spawn")
     with ctx.Pool(workers) as pool:
         parts = pool.map(_run_chunk, jobs)
     S1 = np.zeros(ph.n_vox)
     S2 = np.zeros(ph.n_vox)
+    P2 = np.zeros(ph.nz) if planes else None
     st = {}
-    for s1, s2, d in parts:
+    for s1, s2, p2, d in parts:
         S1 += s1
         S2 += s2
+        if planes:
+            P2 += p2
         for key, val in d.items():
             if key == "max_balance_rel":
                 st[key] = max(st.get(key, 0.0), val)
             else:
                 st[key] = st.get(key, 0) + val
-    return OracleResult(S1, S2, n, st)
+    return OracleResult(S1, S2, n, st, P2)
 
 
 def uncollided(ph, mats_d, pd, src, n, seed) -> int:

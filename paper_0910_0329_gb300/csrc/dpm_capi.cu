@@ -93,7 +93,8 @@ void dfree(dpm_ctx *c, void *p) {
 void free_phantom(dpm_ctx *c, PhantomState *p) {
   if (!p) return;
   drop_events(p);
-  for (void *d : {(void *)p->d_mat, (void *)p->d_rho, (void *)p->d_mumax, (void *)p->d_slabs, (void *)p->d_fslabs,
+  for (void *d : {(void *)p->d_mat, (void *)p->d_rho, (void *)p->d_mumax, (void *)p->d_mumax64, (void *)p->d_slabs,
+                  (void *)p->d_fslabs,
                   (void *)p->d_S1, (void *)p->d_Q, (void *)p->d_counters, (void *)p->d_inv_nb, (void *)p->d_dose,
                   (void *)p->d_sigma, (void *)p->d_dmax})
     dfree(c, d);
@@ -138,6 +139,26 @@ int update_mumax(dpm_ctx *c, PhantomState *p) {
   return DPM_OK;
 }
 
+// The same majorant in FP64 (for the FP64 kernel), made on first use.
+int update_mumax64(dpm_ctx *c, PhantomState *p) {
+  if (p->mumax64_version == c->tables_version) return DPM_OK;
+  const HostTables &t = c->ht;
+  if (!p->d_mumax64) {
+    const int rc = dalloc(c, &p->d_mumax64, size_t(kMaxTableNodes));
+    if (rc) return rc;
+  }
+  std::vector<double> mm(t.n_e, 0.0);
+  for (int i = 0; i < t.n_e; ++i) {
+    double best = 0;
+    for (int m = 0; m <= p->max_mat && m < t.n_mat; ++m)
+      if (p->rho_max[m] > 0) best = std::max(best, p->rho_max[m] * t.mu_mass_nodes[size_t(m) * t.n_e + i]);
+    mm[i] = best * (1.0 + 1e-5);
+  }
+  CUDA_TRY(c, cudaMemcpy(p->d_mumax64, mm.data(), mm.size() * sizeof(double), cudaMemcpyHostToDevice));
+  p->mumax64_version = c->tables_version;
+  return DPM_OK;
+}
+
 uint64_t splitmix(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;
   x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -176,8 +197,10 @@ int ctx_prepare_batches(dpm_ctx *c, PhantomState *p, uint64_t n, int n_batches, 
 
 PhantomState *ctx_phantom(dpm_ctx *c, int id) { return get_phantom(c, id); }
 
-int ctx_run_params(dpm_ctx *c, PhantomState *p, const dpm_source *src, uint64_t first, uint64_t n, uint64_t seed,
-                   int physics_flags, RunParams &R) {
+template <class Real>
+static int fill_run_params(dpm_ctx *c, PhantomState *p, const dpm_source *src, uint64_t first, uint64_t n,
+                           uint64_t seed, int physics_flags, const DevTablesT<Real> &tables, const Real *mu_max,
+                           RunParamsT<Real> &R) {
   if (!src) return fail(c, DPM_EINVAL, "null source");
   if (!c->tables_ready) return fail(c, DPM_ESTATE, "dpm_build_tables() must precede dpm_run()");
   if (p->max_mat >= c->ht.n_mat) return fail(c, DPM_EINVAL, "phantom uses a material index beyond the tables");
@@ -188,39 +211,53 @@ int ctx_run_params(dpm_ctx *c, PhantomState *p, const dpm_source *src, uint64_t 
   if (!(emax > 0) || emax > c->params.e_max) return fail(c, DPM_EINVAL, "source energy outside (0, e_max]");
   if (!(src->sad > 0) || !(src->fx >= 0) || !(src->fy >= 0)) return fail(c, DPM_EINVAL, "bad beam geometry");
   if (n > 0xFFFFFFFFull) return fail(c, DPM_EINVAL, "at most 2^32-1 histories per call");
-  if (physics_flags & ~(DPM_NO_HARD | DPM_NO_MSC)) return fail(c, DPM_EINVAL, "unknown physics flag");
-  R.T = c->dt;
+  if (physics_flags & ~(DPM_NO_HARD | DPM_NO_MSC | DPM_SAUTER)) return fail(c, DPM_EINVAL, "unknown physics flag");
+  R.T = tables;
   R.T.flags = physics_flags;
   R.P.nx = p->nx;
   R.P.ny = p->ny;
   R.P.nz = p->nz;
-  R.P.dx = float(p->dx);
-  R.P.dy = float(p->dy);
-  R.P.dz = float(p->dz);
+  R.P.dx = Real(p->dx);
+  R.P.dy = Real(p->dy);
+  R.P.dz = Real(p->dz);
   R.P.mat = p->d_mat;
   R.P.rho = p->d_rho;
-  R.P.mu_max = p->d_mumax;
+  R.P.mu_max = mu_max;
   const double g = src->gantry_deg * 3.14159265358979323846 / 180.0;
   const double ax[3] = {std::sin(g), 0.0, std::cos(g)};
   R.S.particle = src->particle;
   R.S.spectrum = src->spectrum;
-  R.S.energy = float(src->energy);
-  R.S.sx = float(src->iso[0] - src->sad * ax[0]);
-  R.S.sy = float(src->iso[1] - src->sad * ax[1]);
-  R.S.sz = float(src->iso[2] - src->sad * ax[2]);
-  R.S.cx = float(src->iso[0]);
-  R.S.cy = float(src->iso[1]);
-  R.S.cz = float(src->iso[2]);
-  R.S.e1x = float(std::cos(g));
-  R.S.e1z = float(-std::sin(g));
-  R.S.fx = float(src->fx);
-  R.S.fy = float(src->fy);
+  R.S.energy = Real(src->energy);
+  R.S.sx = Real(src->iso[0] - src->sad * ax[0]);
+  R.S.sy = Real(src->iso[1] - src->sad * ax[1]);
+  R.S.sz = Real(src->iso[2] - src->sad * ax[2]);
+  R.S.cx = Real(src->iso[0]);
+  R.S.cy = Real(src->iso[1]);
+  R.S.cz = Real(src->iso[2]);
+  R.S.e1x = Real(std::cos(g));
+  R.S.e1z = Real(-std::sin(g));
+  R.S.fx = Real(src->fx);
+  R.S.fy = Real(src->fy);
   R.first = first;
   R.n = n;
   const uint64_t k = splitmix(seed);
   R.key0 = uint32_t(k);
   R.key1 = uint32_t(k >> 32);
   return DPM_OK;
+}
+
+int ctx_run_params(dpm_ctx *c, PhantomState *p, const dpm_source *src, uint64_t first, uint64_t n, uint64_t seed,
+                   int physics_flags, RunParams &R) {
+  return fill_run_params(c, p, src, first, n, seed, physics_flags, c->dt, (const float *)p->d_mumax, R);
+}
+
+int ctx_run_params_f64(dpm_ctx *c, PhantomState *p, const dpm_source *src, uint64_t first, uint64_t n,
+                       uint64_t seed, int physics_flags, RunParamsT<double> &R) {
+  if (c->tables_ready) {
+    const int rc = update_mumax64(c, p);
+    if (rc) return rc;
+  }
+  return fill_run_params(c, p, src, first, n, seed, physics_flags, c->dt64, (const double *)p->d_mumax64, R);
 }
 
 }  // namespace dpm
@@ -384,15 +421,16 @@ int dpm_build_tables(dpm_ctx *c, const dpm_material *mats, int n_mat, const dpm_
   const float *ph, *el;
   // device layout of the float4 tables: each node's value followed by the
   // float difference to the next node (see el_at in dpm_device.cuh)
-  auto with_steps = [&](const std::vector<float> &h) {
-    std::vector<float> o(2 * h.size(), 0.f);
+  auto with_steps = [&](const auto &h) {
+    using T = typename std::decay<decltype(h)>::type::value_type;
+    std::vector<T> o(2 * h.size(), T(0));
     for (int m = 0; m < t.n_mat; ++m)
       for (int i = 0; i < t.n_e; ++i)
         for (int k = 0; k < 4; ++k) {
           const size_t at = (size_t(m) * t.n_e + i) * 4 + k;
           o[2 * at - k] = h[at];
           if (i + 1 < t.n_e) {
-            volatile float diff = h[at + 4] - h[at];  // one float subtraction, as on the device
+            volatile T diff = h[at + 4] - h[at];  // one subtraction in the table's type, as on the device
             o[2 * at - k + 4] = diff;
           }
         }
@@ -412,7 +450,8 @@ int dpm_build_tables(dpm_ctx *c, const dpm_material *mats, int n_mat, const dpm_
   };
   if ((rc = samp(t.kn, t.kn_ne, t.kn_lo, t.kn_hi, d.kn)) || (rc = samp(t.mol, t.mol_ne, t.mol_lo, t.mol_hi, d.mol)) ||
       (rc = samp(t.brem, t.brem_ne, t.brem_lo, t.brem_hi, d.brem)) ||
-      (rc = samp(t.pair, t.pair_ne, t.pair_lo, t.pair_hi, d.pair)) || (rc = upload(c, t.msc, &d.msc_lnA)))
+      (rc = samp(t.pair, t.pair_ne, t.pair_lo, t.pair_hi, d.pair)) || (rc = upload(c, t.msc, &d.msc_lnA)) ||
+      (rc = samp(t.sauter, t.sauter_ne, t.sauter_lo, t.sauter_hi, d.sauter)))
     return rc;
   d.msc_n = t.msc_n;
   d.msc_x0 = float(t.msc_x0);
@@ -425,6 +464,48 @@ int dpm_build_tables(dpm_ctx *c, const dpm_material *mats, int n_mat, const dpm_
   d.x_fe = float(std::log1p(-p->f_e) * (t.n_e - 1) / (std::log(t.e_hi) - std::log(t.e_lo)));
   d.x_eabs = float((std::log(p->eabs_e) - std::log(t.e_lo)) * (t.n_e - 1) / (std::log(t.e_hi) - std::log(t.e_lo)));
   c->dt = d;
+  // the FP64 tables for the FP64 kernel
+  {
+    DevTablesT<double> d64{};
+    const double inv = (t.n_e - 1) / (std::log(t.e_hi) - std::log(t.e_lo));
+    d64.n_mat = t.n_mat;
+    d64.n_e = t.n_e;
+    d64.lnE_lo = std::log(t.e_lo);
+    d64.inv_dlnE = inv;
+    d64.x_lg2 = inv * std::log(2.0);
+    d64.x_lo = -std::log(t.e_lo) * inv;
+    const double *ph64, *el64;
+    if ((rc = upload(c, with_steps(t.ph_64), &ph64)) || (rc = upload(c, with_steps(t.el_64), &el64)) ||
+        (rc = upload(c, t.pmol_64, &d64.pmol)))
+      return rc;
+    d64.ph = reinterpret_cast<const Dbl4 *>(ph64);
+    d64.el = reinterpret_cast<const Dbl4 *>(el64);
+    auto samp64 = [&](const std::vector<double> &v, int ne, double lo, double hi, SampTabT<double> &s) {
+      s.ne = ne;
+      s.nu = t.nu;
+      s.lnE0 = std::log(lo);
+      s.inv_dlnE = (ne - 1) / (std::log(hi) - std::log(lo));
+      return upload(c, v, &s.y);
+    };
+    if ((rc = samp64(t.kn_64, t.kn_ne, t.kn_lo, t.kn_hi, d64.kn)) ||
+        (rc = samp64(t.mol_64, t.mol_ne, t.mol_lo, t.mol_hi, d64.mol)) ||
+        (rc = samp64(t.brem_64, t.brem_ne, t.brem_lo, t.brem_hi, d64.brem)) ||
+        (rc = samp64(t.pair_64, t.pair_ne, t.pair_lo, t.pair_hi, d64.pair)) ||
+        (rc = upload(c, t.msc_64, &d64.msc_lnA)) ||
+        (rc = samp64(t.sauter_64, t.sauter_ne, t.sauter_lo, t.sauter_hi, d64.sauter)))
+      return rc;
+    d64.msc_n = t.msc_n;
+    d64.msc_x0 = t.msc_x0;
+    d64.msc_inv_dx = (t.msc_n - 1) / (t.msc_x1 - t.msc_x0);
+    d64.eabs_e = p->eabs_e;
+    d64.eabs_g = p->eabs_g;
+    d64.wcc = p->wcc;
+    d64.wcr = p->wcr;
+    d64.f_e = p->f_e;
+    d64.x_fe = std::log1p(-p->f_e) * inv;
+    d64.x_eabs = (std::log(p->eabs_e) - std::log(t.e_lo)) * inv;
+    c->dt64 = d64;
+  }
   c->params = *p;
   c->tables_ready = true;
   c->tables_version++;
@@ -510,10 +591,14 @@ int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t 
   if (!p) return fail(c, DPM_EINVAL, "bad phantom id");
   dpm_run_opts o{};
   if (opts) o = *opts;
-  if (o.kernel < DPM_KERNEL_QUEUE || o.kernel > DPM_KERNEL_PAPER_CAS) return fail(c, DPM_EINVAL, "unknown kernel");
+  if (o.kernel < DPM_KERNEL_QUEUE || o.kernel > DPM_KERNEL_HISTORY_F64)
+    return fail(c, DPM_EINVAL, "unknown kernel");
   const bool paper = o.kernel == DPM_KERNEL_PAPER_F32 || o.kernel == DPM_KERNEL_PAPER_CAS;
+  const bool f64 = o.kernel == DPM_KERNEL_HISTORY_F64;
   RunParams R{};
-  int rc = ctx_run_params(c, p, src, first, n, seed, o.physics_flags, R);
+  RunParamsT<double> R64{};
+  int rc = f64 ? ctx_run_params_f64(c, p, src, first, n, seed, o.physics_flags, R64)
+               : ctx_run_params(c, p, src, first, n, seed, o.physics_flags, R);
   if (rc) return rc;
   if (n == 0) return DPM_OK;
   cudaSetDevice(c->device);
@@ -538,7 +623,14 @@ int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t 
   for (int i = 0; i < 3; ++i) CUDA_TRY(c, cudaEventCreate(&ev[i]));
   if (p->ev.size() + 3 > kMaxPendingEvents) fold_old_events(p);
   for (int i = 0; i < 3; ++i) p->ev.push_back(ev[i]);
-  if (o.kernel == DPM_KERNEL_HISTORY) {
+  if (f64) {
+    R64.n_batches = B;
+    R64.slabs = p->d_slabs;
+    R64.counters = p->d_counters;
+    R64.err = c->d_err;
+    CUDA_TRY(c, cudaEventRecord(ev[0], c->stream));
+    launch_history_f64(R64, bs, c->sm_count, c->stream);
+  } else if (o.kernel == DPM_KERNEL_HISTORY) {
     CUDA_TRY(c, cudaEventRecord(ev[0], c->stream));
     launch_history(R, bs, c->sm_count, o.block_size, c->stream);
   } else if (paper) {
@@ -734,7 +826,7 @@ int dpm_diag_table(dpm_ctx *c, int which, int mat, int n, const double *energy, 
 int dpm_diag_sample(dpm_ctx *c, int which, double e, double aux, int n, const double *u, double *out) {
   if (!c) return DPM_EINVAL;
   if (!c->tables_ready) return fail(c, DPM_ESTATE, "no tables");
-  if (n < 0 || (n > 0 && (!u || !out)) || which < 0 || which > 8) return fail(c, DPM_EINVAL, "bad arguments");
+  if (n < 0 || (n > 0 && (!u || !out)) || which < 0 || which > 9) return fail(c, DPM_EINVAL, "bad arguments");
   if (n == 0) return DPM_OK;
   cudaSetDevice(c->device);
   double *d = nullptr;

@@ -31,6 +31,8 @@ struct PhantomState {
   float *d_rho = nullptr;
   float *d_mumax = nullptr;  // kMaxTableNodes floats, filled for the current tables
   int mumax_version = -1;
+  double *d_mumax64 = nullptr;  // the FP64 majorant (FP64 runs only), n_e doubles
+  int mumax64_version = -1;
   int max_mat = 0;
   double rho_max[DPM_MAX_MAT] = {0};
   unsigned long long *d_slabs = nullptr;
@@ -68,6 +70,7 @@ struct dpm_ctx {
   dpm_table_params params{};
   dpm::HostTables ht;
   dpm::DevTables dt{};
+  dpm::DevTablesT<double> dt64{};  // the same tables in FP64 (the FP64 kernel)
   std::vector<void *> table_mem;
   std::vector<std::unique_ptr<dpm::PhantomState>> phantoms;
   uint64_t next_phantom_uid = 1;
@@ -94,6 +97,10 @@ PhantomState *ctx_phantom(dpm_ctx *c, int id);
 // batch size are left to the caller).  Allocates nothing.
 int ctx_run_params(dpm_ctx *c, PhantomState *p, const dpm_source *src, uint64_t first, uint64_t n, uint64_t seed,
                    int physics_flags, RunParams &R);
+// The same for the FP64 kernel (FP64 tables, source and majorant; builds the
+// phantom's FP64 majorant on first use).
+int ctx_run_params_f64(dpm_ctx *c, PhantomState *p, const dpm_source *src, uint64_t first, uint64_t n,
+                       uint64_t seed, int physics_flags, RunParamsT<double> &R);
 // Device allocation owned by the context (error message set on failure).
 int ctx_alloc(dpm_ctx *c, void **p, size_t bytes);
 // Batch structure of a run of n histories in (at most) n_batches batches:

@@ -90,6 +90,7 @@ __global__ void k_diag_sample(DevTables T, int which, float e, float aux, int n,
       r = face_dist(x, e, 0, 1.f);
       break;
     }
+    case 9: r = sauter_nu(T, e, lnE, x); break;
     default: r = 0.0;
   }
   out[i] = r;

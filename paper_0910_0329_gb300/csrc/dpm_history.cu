@@ -10,24 +10,27 @@ namespace dpm {
 
 // Tally sink with run-length coalescing: consecutive deposits of one thread
 // into the same voxel are summed in a register and issued as one 64-bit
-// atomic add (exact, order-independent fixed point, 2^-32 MeV).
-struct HistSink {
-  const RunParams &R;
+// atomic add (exact, order-independent fixed point, 2^-32 MeV).  Real: the
+// transport's arithmetic (float; double for the precision ablation).
+template <class Real>
+struct HistSinkT {
+  static constexpr bool kSauter = true;  // DPM_SAUTER compiled in
+  const RunParamsT<Real> &R;
   unsigned long long *slab = nullptr;
   int pend_v = -1;
   long long pend_q = 0;
   long long cnt[C_N];
   int err = 0;
-  Part *stack;
+  PartT<Real> *stack;
   int sp = 0, cap;
 
-  __device__ HistSink(const RunParams &r, Part *st, int c) : R(r), stack(st), cap(c) {
+  __device__ HistSinkT(const RunParamsT<Real> &r, PartT<Real> *st, int c) : R(r), stack(st), cap(c) {
 #pragma unroll
     for (int i = 0; i < C_N; ++i) cnt[i] = 0;
   }
-  __device__ __forceinline__ static long long fx(float e) { return __float2ll_rn(e * 4294967296.0f); }
+  __device__ __forceinline__ static long long fx(Real e) { return Num<Real>::round_ll(e * Real(4294967296.0f)); }
   // energy counters (coarser quantum, see kCounterScale)
-  __device__ __forceinline__ static long long fxc(float e) { return __float2ll_rn(e * kCounterScaleF); }
+  __device__ __forceinline__ static long long fxc(Real e) { return Num<Real>::round_ll(e * Real(kCounterScaleF)); }
   __device__ __forceinline__ void flush() {
     if (pend_v >= 0 && pend_q != 0) {
       atomicAdd(slab + pend_v, (unsigned long long)pend_q);
@@ -36,7 +39,7 @@ struct HistSink {
     pend_v = -1;
     pend_q = 0;
   }
-  __device__ __forceinline__ void deposit(int v, float dE) {
+  __device__ __forceinline__ void deposit(int v, Real dE) {
     const long long q = fx(dE);
     if (v == pend_v) {
       pend_q += q;
@@ -46,14 +49,14 @@ struct HistSink {
       pend_q = q;
     }
   }
-  __device__ __forceinline__ void escape(float E) { cnt[C_ESC] += fxc(E); }
-  __device__ __forceinline__ void push(const Part &q) {
+  __device__ __forceinline__ void escape(Real E) { cnt[C_ESC] += fxc(E); }
+  __device__ __forceinline__ void push(const PartT<Real> &q) {
     ++cnt[C_PUSH];
     if (sp < cap) {
       stack[sp++] = q;
     } else {
       err |= ERR_OVERFLOW;
-      cnt[C_ESC] += fxc(q.E + (q.type == POSITRON ? 2.f * kMc2f : 0.f));
+      cnt[C_ESC] += fxc(q.E + (q.type == POSITRON ? Real(2) * Num<Real>::mc2 : Real(0)));
     }
   }
   __device__ __forceinline__ void error(int e) { err |= e; }
@@ -61,8 +64,10 @@ struct HistSink {
   __device__ __forceinline__ void count_flight() { ++cnt[C_GFLIGHT]; }
   __device__ __forceinline__ void count_interaction() { ++cnt[C_GINT]; }
 };
+using HistSink = HistSinkT<float>;
 
-__device__ void reduce_counters(const long long *cnt, int err, const RunParams &R) {
+template <class RP>
+__device__ void reduce_counters(const long long *cnt, int err, const RP &R) {
 #pragma unroll
   for (int i = 0; i < C_N; ++i) {
     long long v = cnt[i];
@@ -81,24 +86,25 @@ constexpr int kHistStack = 64;
 // 8 resident blocks of 128 threads cap the registers at 64, as in the queue
 // kernel: the extra spills cost less than the doubled occupancy gains
 // (+26 % on 6 MV, +30 % on 20 MeV electrons against 128 registers).
-__global__ void __launch_bounds__(128, 8) k_history(const __grid_constant__ RunParams R, uint64_t batch_size) {
-  Part stack[kHistStack];
-  HistSink s(R, stack, kHistStack);
+template <class Real>
+__global__ void __launch_bounds__(128, 8) k_history(const __grid_constant__ RunParamsT<Real> R, uint64_t batch_size) {
+  PartT<Real> stack[kHistStack];
+  HistSinkT<Real> s(R, stack, kHistStack);
   const size_t V = size_t(R.P.nx) * R.P.ny * R.P.nz;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   for (uint64_t hl = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; hl < R.n; hl += stride) {
     s.slab = R.slabs + (hl / batch_size) * V;
-    Part p;
+    PartT<Real> p;
     const bool hit = make_primary(p, R, uint32_t(hl));
-    s.cnt[C_EMIT] += HistSink::fxc(p.E);
+    s.cnt[C_EMIT] += HistSinkT<Real>::fxc(p.E);
     if (!hit) {
-      s.cnt[C_MISS] += HistSink::fxc(p.E);
+      s.cnt[C_MISS] += HistSinkT<Real>::fxc(p.E);
       continue;
     }
     s.sp = 0;
     s.stack[s.sp++] = p;
     while (s.sp > 0) {
-      Part q = s.stack[--s.sp];
+      PartT<Real> q = s.stack[--s.sp];
       if (q.type == PHOTON) {
         int g = 0;
         while (photon_segment(q, R, s)) {
@@ -124,14 +130,23 @@ __global__ void __launch_bounds__(128, 8) k_history(const __grid_constant__ RunP
   reduce_counters(s.cnt, s.err, R);
 }
 
-void launch_history(const RunParams &R, uint64_t batch_size, int sm_count, int block, cudaStream_t st) {
-  if (block <= 0) block = 128;
-  block = 128;  // the kernel's launch bound
+template <class Real>
+static void launch_history_t(const RunParamsT<Real> &R, uint64_t batch_size, int sm_count, cudaStream_t st) {
+  const int block = 128;  // the kernel's launch bound
   const uint64_t need = (R.n + block - 1) / block;
   const uint64_t cap = uint64_t(sm_count) * 16;
   const int grid = int(need < cap ? need : cap);
-  cudaFuncSetAttribute(k_history, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-  k_history<<<grid > 0 ? grid : 1, block, 0, st>>>(R, batch_size);
+  cudaFuncSetAttribute(k_history<Real>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  k_history<Real><<<grid > 0 ? grid : 1, block, 0, st>>>(R, batch_size);
+}
+
+void launch_history(const RunParams &R, uint64_t batch_size, int sm_count, int block, cudaStream_t st) {
+  (void)block;
+  launch_history_t(R, batch_size, sm_count, st);
+}
+
+void launch_history_f64(const RunParamsT<double> &R, uint64_t batch_size, int sm_count, cudaStream_t st) {
+  launch_history_t(R, batch_size, sm_count, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -168,6 +183,7 @@ __device__ __forceinline__ bool add_f32(float *a, float x) {
 
 template <bool kCas>
 struct PaperSink {
+  static constexpr bool kSauter = false;
   const RunParams &R;
   float *fslab = nullptr;
   int n = 0;

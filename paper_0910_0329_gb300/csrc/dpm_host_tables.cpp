@@ -36,6 +36,7 @@ int dpm_host_tables_get(void *h, const char *name, float *out, int n, double *me
   else if (!std::strcmp(name, "brem")) { v = &t.brem; m[2] = t.brem_ne; m[3] = t.brem_lo; m[4] = t.brem_hi; }
   else if (!std::strcmp(name, "pair")) { v = &t.pair; m[2] = t.pair_ne; m[3] = t.pair_lo; m[4] = t.pair_hi; }
   else if (!std::strcmp(name, "msc")) { v = &t.msc; m[2] = t.msc_n; m[3] = t.msc_x0; m[4] = t.msc_x1; }
+  else if (!std::strcmp(name, "sauter")) { v = &t.sauter; m[2] = t.sauter_ne; m[3] = t.sauter_lo; m[4] = t.sauter_hi; }
   if (!v) return -1;
   if (meta) std::memcpy(meta, m, sizeof(m));
   if (out) std::memcpy(out, v->data(), sizeof(float) * std::min<size_t>(size_t(n), v->size()));

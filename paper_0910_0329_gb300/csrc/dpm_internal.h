@@ -24,50 +24,78 @@ constexpr double kTallyScale = 4294967296.0; // 2^32 fixed-point quanta per MeV
 constexpr double kCounterScale = 16777216.0;  // 2^24 quanta per MeV
 constexpr float kCounterScaleF = 16777216.0f;
 
+// The transport arithmetic is FP32 (Sec. 2.3); an FP64 instantiation of the
+// same code, with FP64 tables, is kept to measure what single precision costs.
+// Four table values of one node in each precision.
+struct alignas(32) Dbl4 {
+  double x, y, z, w;
+};
+template <class Real>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  using type = float4;
+};
+template <>
+struct Vec4<double> {
+  using type = Dbl4;
+};
+
 // One inverse-CDF sampling table: rows on a uniform ln(E) grid, columns on a
 // uniform grid in the uniform deviate u; entries are a normalised variable in
 // [0, 1] whose meaning depends on the process (see dpm_tables.cpp).
-struct SampTab {
-  const float *y;  // [ne][nu]
+template <class Real>
+struct SampTabT {
+  const Real *y;  // [ne][nu]
   int ne, nu;
-  float lnE0, inv_dlnE;
+  Real lnE0, inv_dlnE;
 };
 
 // Device-side view of the tables.  Per-material arrays are [n_mat][n_e].
-struct DevTables {
+template <class Real>
+struct DevTablesT {
+  using V4 = typename Vec4<Real>::type;
   int n_mat, n_e;
-  float lnE_lo, inv_dlnE;
-  float x_lg2, x_lo;  // grid position = log2(E) * x_lg2 + x_lo
+  Real lnE_lo, inv_dlnE;
+  Real x_lg2, x_lo;  // grid position = log2(E) * x_lg2 + x_lo
   // per-material tables [n_mat][n_e][2]: the node's value, then its
   // difference to the next node (zero at the last node)
-  const float4 *ph;    // {mu/rho total (cm^2/g), Compton fraction, photoelectric fraction, 0}
-  const float4 *el;    // {R (g/cm^2), S (MeV cm^2/g), Sigma_hard (cm^2/g), 1/lambda1 (cm^2/g)}
-  const float *pmol;   // Moller fraction of Sigma_hard
-  SampTab kn, mol, brem, pair;
-  const float *msc_lnA;  // ln A on a uniform grid of logit(q)
+  const V4 *ph;    // {mu/rho total (cm^2/g), Compton fraction, photoelectric fraction, 0}
+  const V4 *el;    // {R (g/cm^2), S (MeV cm^2/g), Sigma_hard (cm^2/g), 1/lambda1 (cm^2/g)}
+  const Real *pmol;   // Moller fraction of Sigma_hard
+  SampTabT<Real> kn, mol, brem, pair;
+  const Real *msc_lnA;  // ln A on a uniform grid of logit(q)
   int msc_n;
-  float msc_x0, msc_inv_dx;
-  float eabs_e, eabs_g, wcc, wcr, f_e;
+  Real msc_x0, msc_inv_dx;
+  Real eabs_e, eabs_g, wcc, wcr, f_e;
   int flags;  // DPM_NO_HARD / DPM_NO_MSC
-  float x_fe, x_eabs;  // grid-index shift of an energy step (1 - f_e), grid index of eabs_e
+  Real x_fe, x_eabs;  // grid-index shift of an energy step (1 - f_e), grid index of eabs_e
+  SampTabT<Real> sauter;  // photoelectron angle (option DPM_SAUTER): x/x_max of nu/(A+nu)
 };
 
-struct DevPhantom {
+template <class Real>
+struct DevPhantomT {
   int nx, ny, nz;
-  float dx, dy, dz;
+  Real dx, dy, dz;
   const uint8_t *mat;
   const float *rho;
-  const float *mu_max;  // [n_e] photon majorant, 1/cm, on the tables' energy grid
+  const Real *mu_max;  // [n_e] photon majorant, 1/cm, on the tables' energy grid
 };
 
-struct DevSource {
+template <class Real>
+struct DevSourceT {
   int particle, spectrum;
-  float energy;
-  float sx, sy, sz;        // source point
-  float cx, cy, cz;        // isocentre
-  float e1x, e1z;          // field axis 1 (in the x-z plane); axis 2 is y
-  float fx, fy;
+  Real energy;
+  Real sx, sy, sz;        // source point
+  Real cx, cy, cz;        // isocentre
+  Real e1x, e1z;          // field axis 1 (in the x-z plane); axis 2 is y
+  Real fx, fy;
 };
+
+using SampTab = SampTabT<float>;
+using DevTables = DevTablesT<float>;
+using DevPhantom = DevPhantomT<float>;
+using DevSource = DevSourceT<float>;
 
 // Counters accumulated per thread and reduced at kernel exit.
 enum {
@@ -96,10 +124,11 @@ struct DevJob {
   uint64_t V;
 };
 
-struct RunParams {
-  DevTables T;
-  DevPhantom P;
-  DevSource S;
+template <class Real>
+struct RunParamsT {
+  DevTablesT<Real> T;
+  DevPhantomT<Real> P;
+  DevSourceT<Real> S;
   uint64_t first, n;       // history range
   uint32_t key0, key1;     // Philox key from the seed
   int n_batches;
@@ -110,13 +139,19 @@ struct RunParams {
   int n_jobs;
   int n_photon_jobs;   // the table lists photon-beam jobs first, then electron-beam jobs
 };
+using RunParams = RunParamsT<float>;
 
-// Host-built tables (FP64 closed forms evaluated, stored as FP32).
+// Host-built tables: the closed forms evaluated in FP64 (the *_64 arrays, for
+// the FP64 kernel) and rounded to FP32 (for the transport kernels).
 struct HostTables {
   int n_mat = 0, n_e = 0;
   double e_lo = 0, e_hi = 0;
   std::vector<float> ph, el, pmol;
-  std::vector<float> kn, mol, brem, pair, msc;
+  std::vector<float> kn, mol, brem, pair, msc, sauter;
+  std::vector<double> ph_64, el_64, pmol_64;
+  std::vector<double> kn_64, mol_64, brem_64, pair_64, msc_64, sauter_64;
+  int sauter_ne = 0;
+  double sauter_lo = 0, sauter_hi = 0;
   int kn_ne = 0, mol_ne = 0, brem_ne = 0, pair_ne = 0, nu = 0, msc_n = 0;
   double kn_lo = 0, kn_hi = 0, mol_lo = 0, mol_hi = 0, brem_lo = 0, brem_hi = 0, pair_lo = 0, pair_hi = 0;
   double msc_x0 = 0, msc_x1 = 0;

@@ -8,6 +8,8 @@
 namespace dpm {
 
 void launch_history(const RunParams &R, uint64_t batch_size, int sm_count, int block, cudaStream_t st);
+// The same kernel in FP64 arithmetic with FP64 tables (precision ablation).
+void launch_history_f64(const RunParamsT<double> &R, uint64_t batch_size, int sm_count, cudaStream_t st);
 // The paper's float tally (ablation): transport into float slabs (n_slab
 // floats, zeroed by the caller), then their rounding into R.slabs.
 void launch_history_paper(const RunParams &R, uint64_t batch_size, bool cas, float *fslabs, size_t n_slab,

@@ -149,9 +149,12 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // pushes) for the run statistics; the energy counters (emitted, escaped,
 // missed) are always kept.  The event counts live in registers across the
 // whole loop and cost about 10 % of the transport rate, so runs count them
-// only on request (dpm_run_opts.count_events).
-template <bool kMulti, bool kCount>
+// only on request (dpm_run_opts.count_events).  kSauter_: compile in the
+// photoelectron angle option (DPM_SAUTER); its code alone, unused, measured
+// 4-6 % slower, so only the single-run launches that ask for it carry it.
+template <bool kMulti, bool kCount, bool kSauter_ = false>
 struct QSink {
+  static constexpr bool kSauter = kSauter_;
   const RunParams &R;
   const QDev &Q;
   int home;
@@ -367,9 +370,9 @@ __device__ __forceinline__ JobCtx job_ctx(const RunParams &R, int j) {
 // (batch) from the current job of the batch, job after job, so that one
 // job's phantom and tally are hot in L2 at a time.  A warp holding particles
 // of one type only starts histories of a job with that beam type.
-template <bool kMulti, bool kCount>
+template <bool kMulti, bool kCount, bool kSauter>
 __device__ int refill_source(const RunParams &R, const QDev &Q, unsigned empty, Part &p, bool &alive,
-                             QSink<kMulti, kCount> &sk, int &type) {
+                             QSink<kMulti, kCount, kSauter> &sk, int &type) {
   const int want = __popc(empty);
   if (want == 0) return 0;
   const int lane = threadIdx.x & 31;
@@ -411,8 +414,8 @@ __device__ int refill_source(const RunParams &R, const QDev &Q, unsigned empty, 
       } else {
         hit = make_primary(p, R, uint32_t(hl));
       }
-      sk.cnt[C_EMIT] += QSink<kMulti, kCount>::fxc(p.E);
-      if (!hit) sk.cnt[C_MISS] += QSink<kMulti, kCount>::fxc(p.E);
+      sk.cnt[C_EMIT] += QSink<kMulti, kCount, kSauter>::fxc(p.E);
+      if (!hit) sk.cnt[C_MISS] += QSink<kMulti, kCount, kSauter>::fxc(p.E);
       alive = hit;
     }
   }
@@ -516,7 +519,7 @@ __device__ void reduce_counters_q(const long long *cnt, int err, const RunParams
 #ifndef DPM_QUEUE_MIN_BLOCKS
 #define DPM_QUEUE_MIN_BLOCKS 8
 #endif
-template <bool kMulti, bool kCount>
+template <bool kMulti, bool kCount, bool kSauter = false>
 __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
     k_queue(const __grid_constant__ RunParams R, const __grid_constant__ QDev Q) {
   const int lane = threadIdx.x & 31;
@@ -524,7 +527,7 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
   const int src_type = (R.S.particle == 0) ? 0 : 1;
   const size_t V = size_t(R.P.nx) * R.P.ny * R.P.nz;
   if (lane == 0) atomicAdd(&Q.started->v, 1ull);
-  QSink<kMulti, kCount> sk(R, Q, home);
+  QSink<kMulti, kCount, kSauter> sk(R, Q, home);
   Part p{};
   bool alive = false;
   int nstep = 0;
@@ -558,7 +561,7 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
         } else {
           int ty = S;
           if (refill_queue<kMulti>(Q, S, home, 0, empty, p, alive, sk.err)) mode = S;
-          else if (source_allowed(Q, home, Q.guard[S]) && refill_source<kMulti, kCount>(R, Q, empty, p, alive, sk, ty)) mode = S;
+          else if (source_allowed(Q, home, Q.guard[S]) && refill_source<kMulti, kCount, kSauter>(R, Q, empty, p, alive, sk, ty)) mode = S;
           else if (refill_queue<kMulti>(Q, O, home, 0, empty, p, alive, sk.err)) mode = O;
           else if (refill_queue<kMulti>(Q, O, home, kStealProbes, empty, p, alive, sk.err)) mode = O;
           else if (refill_queue<kMulti>(Q, S, home, kStealProbes, empty, p, alive, sk.err)) mode = S;
@@ -566,7 +569,7 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
       } else if (mode == S) {
         int ty = S;
         if (ph == 0 && !refill_queue<kMulti>(Q, S, home, 0, empty, p, alive, sk.err) && source_allowed(Q, home, Q.guard[S]))
-          refill_source<kMulti, kCount>(R, Q, empty, p, alive, sk, ty);
+          refill_source<kMulti, kCount, kSauter>(R, Q, empty, p, alive, sk, ty);
       } else if (ph == 1 || source_exhausted<kMulti>(R, Q)) {
         refill_queue<kMulti>(Q, O, home, kStealProbes, empty, p, alive, sk.err);
       }
@@ -655,10 +658,11 @@ __global__ void k_queue_init(uint32_t *seq0, uint32_t *seq1, size_t n, uint32_t 
 
 }  // namespace
 
-// The queue kernel's instantiations: batch launch (kMulti) x event counts.
+// The queue kernel's instantiations: batch launch (kMulti) x event counts,
+// and the single-run ones with the photoelectron angle option.
 using QKernel = void (*)(RunParams, QDev);
-const QKernel kQueueKernels[4] = {k_queue<false, false>, k_queue<false, true>, k_queue<true, false>,
-                                  k_queue<true, true>};
+const QKernel kQueueKernels[6] = {k_queue<false, false>,      k_queue<false, true>,      k_queue<true, false>,
+                                  k_queue<true, true>,        k_queue<false, false, true>, k_queue<false, true, true>};
 
 int queue_blocks_per_sm() {
   // the kernel keeps no shared memory: give the whole carveout to L1, where
@@ -699,6 +703,10 @@ size_t queue_bytes(int K, int log2cs) {
 
 int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batch_size, const dpm_run_opts &o,
                  int sm_count, cudaStream_t st, cudaEvent_t start, std::string &err) {
+  if (R.jobs && (R.T.flags & DPM_SAUTER)) {
+    err = "the photoelectron angle option (DPM_SAUTER) runs in single runs only";
+    return DPM_EINVAL;
+  }
   const size_t cs = size_t(1) << log2cs;
   const size_t slots = size_t(K) * cs;
   const size_t per_type = slots * kWordsPerSlot * sizeof(uint32_t) + 2 * size_t(K) * sizeof(Ctl);
@@ -757,9 +765,13 @@ int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batc
   k_queue_init<<<sm_count * 4, 256, 0, st>>>(Q.q[0].seq, Q.q[1].seq, slots, Q.mask);
   if (start) cudaEventRecord(start, st);
   const bool count = o.count_events != 0;
+  const bool sauter = (R.T.flags & DPM_SAUTER) != 0;
   if (R.jobs) {
     if (count) k_queue<true, true><<<K, kQBlock, 0, st>>>(R, Q);
     else k_queue<true, false><<<K, kQBlock, 0, st>>>(R, Q);
+  } else if (sauter) {
+    if (count) k_queue<false, true, true><<<K, kQBlock, 0, st>>>(R, Q);
+    else k_queue<false, false, true><<<K, kQBlock, 0, st>>>(R, Q);
   } else {
     if (count) k_queue<false, true><<<K, kQBlock, 0, st>>>(R, Q);
     else k_queue<false, false><<<K, kQBlock, 0, st>>>(R, Q);

@@ -258,9 +258,9 @@ bool build_tables(const dpm_material *mats, int n_mat, const dpm_table_params &p
   const double l0 = std::log(t.e_lo), dl = (std::log(t.e_hi) - l0) / (N - 1);
   auto node_E = [&](int i) { return std::exp(l0 + i * dl); };
 
-  t.ph.assign(size_t(n_mat) * N * 4, 0.f);
-  t.el.assign(size_t(n_mat) * N * 4, 0.f);
-  t.pmol.assign(size_t(n_mat) * N, 0.f);
+  t.ph_64.assign(size_t(n_mat) * N * 4, 0.0);
+  t.el_64.assign(size_t(n_mat) * N * 4, 0.0);
+  t.pmol_64.assign(size_t(n_mat) * N, 0.0);
   t.mu_mass_nodes.assign(size_t(n_mat) * N, 0.0);
 
   const double kinks[2] = {std::min(p.wcr, 2.0 * p.wcc), std::max(p.wcr, 2.0 * p.wcc)};
@@ -283,17 +283,17 @@ bool build_tables(const dpm_material *mats, int n_mat, const dpm_table_params &p
       photon_mu(M, E, p.c_pe, mc, mpe, mpair);
       double mt = mc + mpe + mpair;
       size_t o = (size_t(m) * N + i) * 4;
-      t.ph[o + 0] = float(mt);
-      t.ph[o + 1] = float(mc / mt);
-      t.ph[o + 2] = float(mpe / mt);
+      t.ph_64[o + 0] = mt;
+      t.ph_64[o + 1] = mc / mt;
+      t.ph_64[o + 2] = mpe / mt;
       t.mu_mass_nodes[size_t(m) * N + i] = mt;
       if (i > 0) R += dR(node_E(i - 1), E);
       double sm = sigma_moller(M, E, p.wcc), sb = sigma_brems(M, E, p.wcr);
-      t.el[o + 0] = float(R);
-      t.el[o + 1] = float(S(E));
-      t.el[o + 2] = float(sm + sb);
-      t.el[o + 3] = float(inv_lambda1(M, E));
-      t.pmol[size_t(m) * N + i] = float(sm + sb > 0 ? sm / (sm + sb) : 0.0);
+      t.el_64[o + 0] = R;
+      t.el_64[o + 1] = S(E);
+      t.el_64[o + 2] = sm + sb;
+      t.el_64[o + 3] = inv_lambda1(M, E);
+      t.pmol_64[size_t(m) * N + i] = sm + sb > 0 ? sm / (sm + sb) : 0.0;
     }
   }
 
@@ -305,7 +305,7 @@ bool build_tables(const dpm_material *mats, int n_mat, const dpm_table_params &p
   // Klein-Nishina: y = ln(eps)/ln(eps0), eps0 = 1/(1+2k)
   row_grid(t.e_lo, t.e_hi, t.kn_lo, t.kn_hi);
   t.kn_ne = NR;
-  t.kn.assign(size_t(NR) * NU, 0.f);
+  t.kn_64.assign(size_t(NR) * NU, 0.0);
   for (int r = 0; r < NR; ++r) {
     double E = std::exp(std::log(t.kn_lo) + r * (std::log(t.kn_hi) - std::log(t.kn_lo)) / (NR - 1));
     double k = E / kMc2, e0 = 1.0 / (1.0 + 2.0 * k), P0 = kn_prim(k, e0), P1 = kn_prim(k, 1.0);
@@ -314,14 +314,14 @@ bool build_tables(const dpm_material *mats, int n_mat, const dpm_table_params &p
       if (c == 0) e = e0;
       else if (c == NU - 1) e = 1.0;
       else e = std::exp(invert([&](double le) { return (kn_prim(k, std::exp(le)) - P0) / (P1 - P0); }, std::log(e0), 0.0, u));
-      t.kn[size_t(r) * NU + c] = float(std::log(e) / std::log(e0));
+      t.kn_64[size_t(r) * NU + c] = std::log(e) / std::log(e0);
     }
   }
 
   // Moller: z = (1/ec - 1/eps)/(1/ec - 2), eps = W/T in [ec, 1/2], ec = wcc/T
   row_grid(2.0 * p.wcc * 1.0001, t.e_hi, t.mol_lo, t.mol_hi);
   t.mol_ne = NR;
-  t.mol.assign(size_t(NR) * NU, 0.f);
+  t.mol_64.assign(size_t(NR) * NU, 0.0);
   for (int r = 0; r < NR; ++r) {
     double T = std::exp(std::log(t.mol_lo) + r * (std::log(t.mol_hi) - std::log(t.mol_lo)) / (NR - 1));
     Kin k(T);
@@ -332,14 +332,14 @@ bool build_tables(const dpm_material *mats, int n_mat, const dpm_table_params &p
       if (c == 0) e = ec;
       else if (c == NU - 1) e = 0.5;
       else e = invert([&](double x) { return (moller_prim(a, b, x) - P0) / (P1 - P0); }, ec, 0.5, u);
-      t.mol[size_t(r) * NU + c] = float((1.0 / ec - 1.0 / e) / (1.0 / ec - 2.0));
+      t.mol_64[size_t(r) * NU + c] = (1.0 / ec - 1.0 / e) / (1.0 / ec - 2.0);
     }
   }
 
   // bremsstrahlung: y = ln(k/wcr)/ln(T/wcr)
   row_grid(p.wcr * 1.0001, t.e_hi, t.brem_lo, t.brem_hi);
   t.brem_ne = NR;
-  t.brem.assign(size_t(NR) * NU, 0.f);
+  t.brem_64.assign(size_t(NR) * NU, 0.0);
   for (int r = 0; r < NR; ++r) {
     double T = std::exp(std::log(t.brem_lo) + r * (std::log(t.brem_hi) - std::log(t.brem_lo)) / (NR - 1));
     double E = T + kMc2, P0 = brems_prim(E, p.wcr), P1 = brems_prim(E, T);
@@ -349,14 +349,14 @@ bool build_tables(const dpm_material *mats, int n_mat, const dpm_table_params &p
       else if (c == NU - 1) kk = T;
       else kk = std::exp(invert([&](double lk) { return (brems_prim(E, std::exp(lk)) - P0) / (P1 - P0); },
                                 std::log(p.wcr), std::log(T), u));
-      t.brem[size_t(r) * NU + c] = float(std::log(kk / p.wcr) / std::log(T / p.wcr));
+      t.brem_64[size_t(r) * NU + c] = std::log(kk / p.wcr) / std::log(T / p.wcr);
     }
   }
 
   // pair: y = (eps - lo)/(hi - lo) on the support of the clamped shape
   row_grid(2.0 * std::exp(0.5) * kMc2 * 1.0001, std::max(t.e_hi, 2.0 * std::exp(0.5) * kMc2 * 1.01), t.pair_lo, t.pair_hi);
   t.pair_ne = NR;
-  t.pair.assign(size_t(NR) * NU, 0.f);
+  t.pair_64.assign(size_t(NR) * NU, 0.0);
   {
     const int NF = 4096;
     std::vector<double> cum(NF + 1);
@@ -364,7 +364,7 @@ bool build_tables(const dpm_material *mats, int n_mat, const dpm_table_params &p
       double E = std::exp(std::log(t.pair_lo) + r * (std::log(t.pair_hi) - std::log(t.pair_lo)) / (NR - 1));
       double k = E / kMc2, lo, hi;
       if (!pair_support(k, lo, hi)) {
-        for (int c = 0; c < NU; ++c) t.pair[size_t(r) * NU + c] = float(double(c) / (NU - 1));
+        for (int c = 0; c < NU; ++c) t.pair_64[size_t(r) * NU + c] = double(c) / (NU - 1);
         continue;
       }
       // cumulative integral on a fine grid (Simpson per cell with the midpoint)
@@ -380,7 +380,44 @@ bool build_tables(const dpm_material *mats, int n_mat, const dpm_table_params &p
         j = std::min(std::max(j, 1), NF);
         double f = (cum[j] > cum[j - 1]) ? (target - cum[j - 1]) / (cum[j] - cum[j - 1]) : 0.0;
         double e = lo + (j - 1 + f) * h;
-        t.pair[size_t(r) * NU + c] = float(std::min(1.0, std::max(0.0, (e - lo) / (hi - lo))));
+        t.pair_64[size_t(r) * NU + c] = std::min(1.0, std::max(0.0, (e - lo) / (hi - lo)));
+      }
+    }
+  }
+
+  // Sauter photoelectron angle (option DPM_SAUTER): in x = nu/(A+nu),
+  // nu = 1 - cos(theta), A = 1/beta - 1, Sauter's K-shell distribution is
+  // p(x) ~ x (2 - (2+A) x) (1 + A B/(1-x)) on [0, 2/(2+A)], B = beta g(g-1)(g-2)/2;
+  // y = x / x_max, rows on ln T of the photoelectron, columns uniform in
+  // w = acos(1 - 2u)/pi: the density vanishes linearly at both ends of x,
+  // so x ~ sqrt(u) and x_max - x ~ sqrt(1-u) there, and in w both ends are
+  // linear (a table uniform in u would be steep at the ends)
+  row_grid(p.eabs_e, t.e_hi, t.sauter_lo, t.sauter_hi);
+  t.sauter_ne = NR;
+  t.sauter_64.assign(size_t(NR) * NU, 0.0);
+  {
+    const int NF = 4096;
+    std::vector<double> cum(NF + 1);
+    for (int r = 0; r < NR; ++r) {
+      const double T = std::exp(std::log(t.sauter_lo) + r * (std::log(t.sauter_hi) - std::log(t.sauter_lo)) / (NR - 1));
+      const Kin k(T);
+      const double beta = std::sqrt(k.beta2), A = 1.0 / beta - 1.0;
+      const double B = 0.5 * beta * k.gam * (k.gam - 1.0) * (k.gam - 2.0);
+      const double xm = 2.0 / (2.0 + A);
+      auto px = [&](double x) { return x * (2.0 - (2.0 + A) * x) * (1.0 + A * B / (1.0 - x)); };
+      const double h = xm / NF;
+      cum[0] = 0;
+      for (int j = 0; j < NF; ++j) {
+        const double a = j * h;
+        cum[j + 1] = cum[j] + h / 6.0 * (px(a) + 4.0 * px(a + 0.5 * h) + px(a + h));
+      }
+      for (int c = 0; c < NU; ++c) {
+        const double u = 0.5 * (1.0 - std::cos(kPi * double(c) / (NU - 1)));
+        const double target = cum[NF] * u;
+        int j = int(std::lower_bound(cum.begin(), cum.end(), target) - cum.begin());
+        j = std::min(std::max(j, 1), NF);
+        const double f = (cum[j] > cum[j - 1]) ? (target - cum[j - 1]) / (cum[j] - cum[j - 1]) : 0.0;
+        t.sauter_64[size_t(r) * NU + c] = std::min(1.0, std::max(0.0, (j - 1 + f) / NF));
       }
     }
   }
@@ -389,13 +426,27 @@ bool build_tables(const dpm_material *mats, int n_mat, const dpm_table_params &p
   t.msc_n = 1025;
   t.msc_x0 = -24.0;
   t.msc_x1 = 24.0;
-  t.msc.assign(t.msc_n, 0.f);
+  t.msc_64.assign(t.msc_n, 0.0);
   for (int i = 0; i < t.msc_n; ++i) {
     double x = t.msc_x0 + i * (t.msc_x1 - t.msc_x0) / (t.msc_n - 1);
     double q = 1.0 / (1.0 + std::exp(-x));
     double lA = invert([&](double la) { return hinge_mean(std::exp(la)); }, -120.0, 80.0, q);
-    t.msc[i] = float(lA);
+    t.msc_64[i] = lA;
   }
+  // the FP32 tables of the transport kernels: each value rounded once
+  auto to_f32 = [](const std::vector<double> &d, std::vector<float> &f) {
+    f.resize(d.size());
+    for (size_t i = 0; i < d.size(); ++i) f[i] = float(d[i]);
+  };
+  to_f32(t.ph_64, t.ph);
+  to_f32(t.el_64, t.el);
+  to_f32(t.pmol_64, t.pmol);
+  to_f32(t.kn_64, t.kn);
+  to_f32(t.mol_64, t.mol);
+  to_f32(t.brem_64, t.brem);
+  to_f32(t.pair_64, t.pair);
+  to_f32(t.msc_64, t.msc);
+  to_f32(t.sauter_64, t.sauter);
   return true;
 }
 

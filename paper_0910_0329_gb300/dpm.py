@@ -20,8 +20,8 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "
 
 DPM_OK, DPM_EINVAL, DPM_ENOMEM, DPM_ECUDA, DPM_EQUEUE_OVERFLOW, DPM_ETIMEOUT, DPM_ESTATE = 0, -1, -2, -3, -4, -5, -6
 DPM_ESTEPCAP = -7
-KERNEL_QUEUE, KERNEL_HISTORY, KERNEL_PAPER_F32, KERNEL_PAPER_CAS = 0, 1, 2, 3
-NO_HARD, NO_MSC = 1, 2
+KERNEL_QUEUE, KERNEL_HISTORY, KERNEL_PAPER_F32, KERNEL_PAPER_CAS, KERNEL_HISTORY_F64 = 0, 1, 2, 3, 4
+NO_HARD, NO_MSC, SAUTER = 1, 2, 4
 _NAMES = {0: "DPM_OK", -1: "DPM_EINVAL", -2: "DPM_ENOMEM", -3: "DPM_ECUDA", -4: "DPM_EQUEUE_OVERFLOW",
           -5: "DPM_ETIMEOUT", -6: "DPM_ESTATE", -7: "DPM_ESTEPCAP"}
 

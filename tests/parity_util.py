@@ -34,3 +34,32 @@ def compare(ph, dose_g, sigma_g, raw_g, n_g, orc, frac_cut=0.1):
         "e_rel_diff": (e_g - e_o) / e_o,
         "e_rel_sigma": math.sqrt(se_o ** 2 + se_g ** 2) / e_o,
     }
+
+
+def compare_planes(ph, raw_g, n_g, orc, frac_cut=0.1):
+    """Depth-dose integrated over each z plane: the GPU's and the oracle's
+    energy per history in every plane with more than frac_cut of the largest
+    plane's, z = (E_gpu - E_oracle) / sigma with the oracle's history-by-history
+    standard deviation of the plane energy scaled to both history counts (the
+    same physics on both sides), and the relative differences of the planes
+    whose combined 2 sigma is below 0.2 %."""
+    nz = ph.nz
+    e_o, se_o = orc.plane_energy_and_sigma(nz)
+    sd_h = se_o * math.sqrt(max(orc.n - 1, 1))  # per-history standard deviation
+    e_g = raw_g.reshape(nz, -1).sum(axis=1).astype(np.float64) / 2.0 ** 32 / n_g
+    sel = e_o > frac_cut * e_o.max()
+    sig = sd_h[sel] * math.sqrt(1.0 / orc.n + 1.0 / n_g)
+    z = (e_g[sel] - e_o[sel]) / sig
+    rel = (e_g[sel] - e_o[sel]) / e_o[sel]
+    tight = 2 * sig / e_o[sel] < 0.2e-2
+    return {
+        "n_planes": int(sel.sum()),
+        "pass_frac": float(np.mean(np.abs(z) <= 2.0)),
+        "z_max": float(np.abs(z).max()),
+        "z_mean": float(z.mean()),
+        "chi2_per_plane": float(np.mean(z * z)),
+        "z": [round(float(x), 2) for x in z],
+        "rel_sigma_median": float(np.median(sig / e_o[sel])),
+        "n_tight": int(tight.sum()),
+        "rel_max_tight": float(np.abs(rel[tight]).max()) if tight.any() else 0.0,
+    }

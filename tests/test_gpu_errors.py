@@ -154,3 +154,13 @@ def test_device_memory_budget_of_a_context(gpu_lib):
         pid = d.load_phantom(wl.phantom)
         d.run(pid, wl.source, 2000, wl.seed)
         assert d.read(pid)[2].sum() > 0
+
+
+def test_sauter_option_is_single_run_only(gpu_lib):
+    wl = W.c1_photon_wbw()
+    with dpm.Dpm(0, W.MATERIALS, wl.params) as d:
+        pid = d.load_phantom(wl.phantom)
+        assert code_of(dpm.dpm_run_batch, d.ctx, [(pid, wl.source, 0, 100, 1)],
+                       dpm.run_opts(physics_flags=dpm.SAUTER)) == dpm.DPM_EINVAL
+        d.run(pid, wl.source, 1000, 1, physics_flags=dpm.SAUTER)  # a single run takes it
+        assert d.read(pid)[2].sum() > 0

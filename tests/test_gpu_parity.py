@@ -5,6 +5,7 @@ per history agrees within 0.2 %.  The oracle runs with history-by-history
 variance; the GPU with the batch method.  History counts are chosen so that
 the combined standard error of the integral is well below 0.2 %."""
 import dataclasses
+import math
 import os
 
 import numpy as np
@@ -14,7 +15,7 @@ from oracle import oracle as O
 from paper_0910_0329_gb300 import dpm
 from paper_0910_0329_gb300 import workloads as W
 
-from parity_util import compare
+from parity_util import compare, compare_planes
 
 pytestmark = pytest.mark.gpu
 KERNELS = [dpm.KERNEL_HISTORY, dpm.KERNEL_QUEUE]
@@ -57,6 +58,12 @@ CASES = {
     "e20_oblique35_wlw": (oblique_electrons, 80000, 800000),
     "e20_wbw_61x61x60": (electrons_bone, 80000, 800000),
     "6mv_wlw_61x61x60": (photons_lung, 6_000_000, 30_000_000),
+    # the paper's own geometry (Sec. 3, Table 1): 61 x 61 x 150 voxels of
+    # 0.5 x 0.5 x 0.2 cm, water 0-5 / lung or bone 5-10 / water 10-30 cm, SSD 90
+    # (0.2 cm voxels hold fewer deposits each: more histories on both sides
+    # keep the voxel z statistic near its normal limit)
+    "paper_e20_wlw_61x61x150": (lambda: W.paper_case(W.ELECTRON, "lung"), 240000, 2400000),
+    "paper_6mv_wbw_61x61x150": (lambda: W.paper_case(W.PHOTON, "bone"), 6_000_000, 30_000_000),
 }
 
 _oracle_cache = {}
@@ -67,7 +74,7 @@ def oracle_result(name):
         make, n_o, _ = CASES[name]
         wl = make()
         _oracle_cache[name] = (wl, O.run(wl.phantom, W.MATERIALS, wl.params, wl.source, n_o, 1000 + wl.seed,
-                                         workers=WORKERS))
+                                         workers=WORKERS, planes=True))
     return _oracle_cache[name]
 
 
@@ -95,6 +102,72 @@ def test_dose_parity(name, kernel):
     assert abs(r["e_rel_diff"]) < 0.2e-2, r
     bal = abs(st["emitted"] - st["deposited"] - st["escaped"] - st["missed"]) / st["emitted"]
     assert bal < 1e-5
+    # the depth dose integrated over lateral planes, where a per-history
+    # skew averages out and a depth bias of a few 0.1 % would show: every
+    # plane within 4 sigma, the mean of z^2 within 4 of its standard
+    # deviations (sqrt(2/n)) of 1, and within 0.2 % wherever 2 sigma is below
+    # 0.2 %.  (Neighbouring planes share histories, so the planes' z are
+    # correlated: a fraction-within-2-sigma gate on 25-60 planes would fail
+    # by chance too often to be a test.)
+    pr = compare_planes(wl.phantom, raw, n_g, orc)
+    print(name, kernel, pr)
+    assert pr["n_planes"] >= 10
+    assert pr["z_max"] < 4.0, pr
+    assert pr["chi2_per_plane"] < 1.0 + 4.0 * math.sqrt(2.0 / pr["n_planes"]), pr
+    assert pr["rel_max_tight"] <= 0.2e-2, pr
+
+
+# GPU against GPU with the parity cases' history counts (GPU run against a
+# smaller GPU run of another seed in place of the oracle), for the mean z of
+# the voxel comparison
+CONTROL = ["6mv_wbw_61x61x60", "e20_blob128"]
+
+
+@pytest.mark.parametrize("name", CONTROL)
+def test_mean_z_is_reproduced_gpu_against_gpu(name):
+    """The voxel z statistic has a small positive mean in the parity runs
+    (per-history deposits are skewed, so a voxel's estimated sigma grows with
+    its estimated dose, most in the smaller sample).  The same comparison
+    with a second, smaller GPU run (another seed, the oracle's history count
+    and 1000 batches, so that its sigma tracks the history-by-history one) in
+    place of the oracle must reproduce that mean within the standard errors:
+    the GPU-oracle mean z is the statistic's, not a dose bias."""
+    wl, orc = oracle_result(name)
+    _, n_o, n_g = CASES[name]
+    dose, sigma, raw, st = gpu_run(wl, n_g, dpm.KERNEL_QUEUE)
+    r_orc = compare(wl.phantom, dose, sigma, raw, n_g, orc)
+    d2, s2, _, _ = gpu_run(wl, n_o, dpm.KERNEL_QUEUE, seed=wl.seed + 7919, n_batches=1000, first=10 ** 9)
+    sel = dose > 0.1 * dose.max()
+    z = (dose[sel] - d2[sel]) / np.sqrt(sigma[sel] ** 2 + s2[sel] ** 2 + 1e-300)
+    se = math.sqrt(r_orc["z_std"] ** 2 / r_orc["n_vox"] + z.std() ** 2 / z.size)
+    print(name, "GPU-oracle", r_orc["z_mean"], "GPU-GPU", z.mean(), "se", se)
+    assert z.mean() > 0 and r_orc["z_mean"] > 0
+    assert abs(z.mean() - r_orc["z_mean"]) < 4 * se, (z.mean(), r_orc["z_mean"], se)
+
+
+@pytest.mark.parametrize("kernel", KERNELS, ids=["history", "queue"])
+def test_sauter_photoelectrons_parity(kernel):
+    """Photoelectrons at Sauter's polar angle (DPM_SAUTER on the GPU,
+    OR_SAUTER in the oracle): a 400 keV photon beam of 4 x 4 cm in bone,
+    where photoelectrons above the 200 keV absorption energy are the most
+    frequent (the photoelectric share of interactions grows as Z^4/E^3).  The
+    field is wide enough for ~10^4 voxels above 5 % of D_max, so that the
+    within-2-sigma fraction (expected 95.45 %) is measured to about 0.2 %."""
+    ph = W.slab_phantom(41, 41, 48, 0.25, [(0, 1e9, W.MAT_BONE, 1.85)])
+    X, Y, _ = ph.extent
+    src = W.Source(W.PHOTON, W.SPEC_MONO, 0.4, (X / 2, Y / 2, 0.0), 100.0, 4.0, 4.0)
+    wl = W.Workload("sauter", ph, src, 0, 41, dict(W.DEFAULT_PARAMS))
+    orc = O.run(ph, W.MATERIALS, wl.params, src, 10_000_000, 43, workers=WORKERS, flags=O.OR_SAUTER)
+    n = 100_000_000
+    with dpm.Dpm(0, W.MATERIALS, wl.params) as d:
+        pid = d.load_phantom(ph)
+        d.run(pid, src, n, wl.seed, kernel=kernel, physics_flags=dpm.SAUTER, count_events=1)
+        dose, sigma, raw, st = d.read(pid)
+    assert st["error_flags"] == 0
+    r = compare(ph, dose, sigma, raw, n, orc, frac_cut=0.05)
+    print("sauter", kernel, r)
+    assert r["n_vox"] > 5000
+    assert r["pass_frac"] >= 0.95 and abs(r["e_rel_diff"]) < max(0.2e-2, 3 * r["e_rel_sigma"]), r
 
 
 _pair_cache = {}

@@ -133,3 +133,24 @@ def test_face_distance(tables_ctx):
         ref = np.maximum(ref, 0.0)
         assert np.all(got >= 0.0)
         assert np.all(np.abs(got - ref) <= 6 * 2.0 ** -24 * ref + 1e-30), (c, np.max(np.abs(got - ref) / np.maximum(ref, 1e-30)))
+
+
+def _sauter_cdf_nu(T, nu):
+    """CDF in nu = 1 - cos(theta) of Sauter's photoelectron distribution,
+    integrated in cos(theta) from the formula in the polar angle."""
+    g = 1 + T / MC2
+    b = np.sqrt(1 - 1 / g ** 2)
+    f = lambda c: (1 - c * c) / (1 - b * c) ** 4 * (1 + 0.5 * g * (g - 1) * (g - 2) * (1 - b * c))
+    tot = quad(f, -1, 1)
+    return np.array([quad(f, 1 - x, 1) / tot for x in nu])
+
+
+@pytest.mark.parametrize("T", [0.25, 1.0, 5.0, 19.0])
+def test_sauter(tables_ctx, T):
+    """The device's Sauter photoelectron angle (table in acos(1 - 2u)/pi,
+    FP32) against Sauter's formula integrated in the polar angle: the CDF at
+    the sampled 1 - cos(theta) returns u."""
+    nu = dpm.dpm_diag_sample(tables_ctx.ctx, 9, T, 0.0, U)
+    assert nu.min() >= 0 and nu.max() <= 2 + 1e-6
+    F = _sauter_cdf_nu(T, nu)
+    assert np.max(np.abs(F - U)) < 2e-4

@@ -189,3 +189,32 @@ def test_msc_table(tabs):
         i = int(t)
         A = math.exp(ms[i] + (ms[i + 1] - ms[i]) * (t - i))
         assert A == pytest.approx(L.or_msc_A(q), rel=2e-5)
+
+
+def _sauter_cdf_nu(T, nu):
+    """CDF in nu = 1 - cos(theta) of Sauter's photoelectron distribution,
+    integrated in cos(theta) from the formula in the polar angle."""
+    g = 1 + T / MC2
+    b = math.sqrt(1 - 1 / g ** 2)
+    f = lambda c: (1 - c * c) / (1 - b * c) ** 4 * (1 + 0.5 * g * (g - 1) * (g - 2) * (1 - b * c))
+    a = 1 / b - 1
+    pts = [1 - a, 1 - 3 * a] if a < 0.3 else None
+    tot = integrate.quad(f, -1, 1, epsabs=0, epsrel=1e-11, limit=400, points=pts)[0]
+    return np.array([integrate.quad(f, 1 - x, 1, epsabs=0, epsrel=1e-10, limit=400)[0] / tot for x in nu])
+
+
+def test_sauter_table(tabs):
+    """The Sauter table (x / x_max of nu/(A+nu) against u, built from the
+    density in x) inverts the distribution written in theta: at the sampled
+    nu the CDF returns u within the bilinear interpolation error."""
+    sa, sm = tabs.get("sauter")
+    assert sm[3] == pytest.approx(P["eabs_e"])
+    for T in [0.21, 0.5, 1.5, 6.0, 19.0]:
+        g = 1 + T / MC2
+        A = 1 / math.sqrt(1 - 1 / g ** 2) - 1
+        w = np.arccos(1 - 2 * U) / math.pi  # the table's columns are uniform in w
+        x = samp(sa, sm, T, w) * 2 / (2 + A)
+        nu = A * x / (1 - x)
+        assert nu.min() >= 0 and nu.max() <= 2
+        F = _sauter_cdf_nu(T, nu)
+        assert np.abs(F - U).max() < 1e-4, (T, np.abs(F - U).max())

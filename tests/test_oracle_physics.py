@@ -437,3 +437,38 @@ def test_water_collision_stopping_power_with_density_effect_textbook(L):
     assert L.or_scol(w, 1.0, 1.0) == pytest.approx(1.849, rel=0.01)
     assert L.or_scol(w, 10.0, 10.0) == pytest.approx(1.968, rel=0.02)
     assert L.or_scol(w, 10.0, 10.0) < L.or_scol(WATER, 10.0, 10.0) * 0.92
+
+
+def sauter_dcos(T, cth):
+    """Sauter's K-shell photoelectron distribution per unit cos(theta), written
+    in the polar angle (the form the oracle's sampler is NOT written in):
+    sin^2/(1 - b cos)^4 [1 + g(g-1)(g-2)(1 - b cos)/2]."""
+    g = 1 + T / MC2
+    b = math.sqrt(1 - 1 / g ** 2)
+    return (1 - cth ** 2) / (1 - b * cth) ** 4 * (1 + 0.5 * g * (g - 1) * (g - 2) * (1 - b * cth))
+
+
+@pytest.mark.parametrize("T", [0.05, 0.3, 1.0, 5.0])
+def test_sauter_sampler_chi2(T):
+    # the sampler draws nu = 1 - cos(theta) by rejection in the variable
+    # x = nu/(A+nu); the bins' probabilities integrate Sauter's formula in cos(theta)
+    s = O.sample(O.S_SAUTER, T, 0, 200000, seed=19)
+    assert s.min() >= 0 and s.max() <= 2
+    cth = 1 - s
+    # bins in 1 - cos: geometric near the forward peak, which narrows with energy
+    g = 1 + T / MC2
+    a = 1 / math.sqrt(1 - 1 / g ** 2) - 1
+    edges_nu = np.concatenate([[0.0], np.geomspace(a / 50, 2.0, 40)])
+    probs = np.array([quad(lambda c: sauter_dcos(T, c), 1 - hi, 1 - lo) for lo, hi in zip(edges_nu[:-1], edges_nu[1:])])
+    assert chi2_p(s, edges_nu, probs) > 0.01
+    assert np.all(np.isfinite(cth))
+
+
+def test_sauter_low_energy_limit_is_the_dipole():
+    # b -> 0: the distribution tends to sin^2(theta), so <cos> -> 0 and
+    # <cos^2> -> 1/5 (the dipole's moments); at 1 keV the 4 b cos correction is
+    # visible in <cos> (about +4b/5 for small b), so test at 10 eV
+    s = O.sample(O.S_SAUTER, 1e-5, 0, 400000, seed=23)
+    c = 1 - s
+    assert abs(c.mean()) < 0.01
+    assert c.var() + c.mean() ** 2 == pytest.approx(0.2, abs=0.005)

@@ -168,3 +168,27 @@ def test_density_effect_transport_conserves_energy_and_lengthens_ranges():
     w, w0 = O.material(MATERIALS_DE[0]), O.material(W.WATER)
     assert L.or_csda_path(w, pr, 0.2, 0.44) == pytest.approx(L.or_csda_path(w0, pr, 0.2, 0.44), rel=1e-12)
     assert L.or_csda_path(w, pr, 0.2, 20.0) > 1.05 * L.or_csda_path(w0, pr, 0.2, 20.0)
+
+
+def test_plane_second_moments_by_brute_force():
+    """The per-plane second moment P2 of a run equals, history by history, the
+    square of each history's plane energies (each history run on its own, so
+    its S1 is that history's deposits), summed; a one-voxel column (each plane
+    one voxel) gives P2 = S2 exactly; and the plane sigma is non-negative."""
+    ph = W.slab_phantom(5, 4, 12, 0.4, [(0, 2, W.MAT_WATER, 1.0), (2, 3, W.MAT_BONE, 1.85),
+                                        (3, 1e9, W.MAT_LUNG, 0.3)])
+    src = dataclasses.replace(pencil(ph, W.ELECTRON, 4.0), fx=1.5, fy=1.2)
+    n = 60
+    r = O.run(ph, W.MATERIALS, P, src, n, 11, workers=1, planes=True)
+    brute = np.zeros(ph.nz)
+    for h in range(n):
+        one = O.run(ph, W.MATERIALS, P, src, 1, 11, h0=h, workers=1)
+        brute += one.S1.reshape(ph.nz, -1).sum(axis=1) ** 2
+    assert brute.sum() > 0
+    np.testing.assert_allclose(r.P2, brute, rtol=1e-12, atol=1e-300)
+    e, s = r.plane_energy_and_sigma(ph.nz)
+    np.testing.assert_allclose(e, r.S1.reshape(ph.nz, -1).sum(axis=1) / n, rtol=1e-14)
+    assert (s >= 0).all() and s.max() > 0
+    col = water_slab(30, 0.2)
+    rc = O.run(col, W.MATERIALS, P, pencil(col, W.ELECTRON, 3.0), 40, 3, workers=2, planes=True)
+    np.testing.assert_allclose(rc.P2, rc.S2, rtol=1e-12)
