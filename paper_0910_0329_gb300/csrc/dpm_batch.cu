@@ -18,7 +18,10 @@ using namespace dpm;
 
 namespace {
 
-constexpr uint64_t kSoloHistories = 1000000;
+#ifndef DPM_SOLO_HISTORIES
+#define DPM_SOLO_HISTORIES 3000000
+#endif
+constexpr uint64_t kSoloHistories = DPM_SOLO_HISTORIES;
 
 #define BATCH_TRY(ctx, call)                                                                   \
   do {                                                                                         \
@@ -81,9 +84,11 @@ extern "C" int dpm_run_batch(dpm_ctx *c, const dpm_job *jobs, int n_jobs, const 
   // and hot tally slab (13 bytes per voxel) exceed a quarter of L2 -- two
   // such jobs overlapping at a job boundary evict each other (13-15 % slower
   // on 256x256x128 phantoms) -- or when it has kSoloHistories or more: the
-  // shared launch pays for the job-table indirection on every step and only
-  // gains from filling short jobs' tails (64-job batch: all shared 1133 ms,
-  // all separate 1059 ms, split at 10^6 histories 1048 ms).
+  // shared launch reads each particle's job record on every step and only
+  // gains from filling short jobs' start-up and drain.  With the records in
+  // shared memory the 64-job batch measured 741 / 732 / 730 / 731 / 751 ms
+  // with the split at 1, 2, 3, 5 and 10 million histories (755 ms as 64
+  // separate runs).
   int l2 = 0;
   cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device);
   const size_t solo_bytes = size_t(l2 > 0 ? l2 : (96 << 20)) / 4;
@@ -101,7 +106,8 @@ extern "C" int dpm_run_batch(dpm_ctx *c, const dpm_job *jobs, int n_jobs, const 
     int B = 0;
     if ((rc = ctx_prepare_batches(c, p, jobs[j].n_histories, o.n_batches, bs, B))) return rc;
     b.total += Rj.n;
-    if (p->V * 13 > solo_bytes || jobs[j].n_histories >= kSoloHistories) {
+    // (beyond kSharedJobs small jobs, the rest run on their own as well)
+    if (p->V * 13 > solo_bytes || jobs[j].n_histories >= kSoloHistories || int(b.tab.size()) >= kSharedJobs) {
       Rj.n_batches = B;
       Rj.slabs = p->d_slabs;
       Rj.err = c->d_err;
@@ -293,7 +299,10 @@ extern "C" int dpm_batch_stats(dpm_ctx *c, dpm_run_stats *st) {
   for (cudaEvent_t e : c->batch_ev) cudaEventDestroy(e);
   c->batch_ev.clear();
   c->batch_histories = 0;
-  st->error_flags = sync_rc == DPM_OK ? 0 : (sync_rc == DPM_EQUEUE_OVERFLOW ? 1 : 4);
+  st->error_flags = sync_rc == DPM_OK                ? 0
+                    : sync_rc == DPM_EQUEUE_OVERFLOW ? 1
+                    : sync_rc == DPM_ESTEPCAP        ? 2
+                                                     : 4;
   if (sync_rc) c->err = keep;
   return sync_rc;
 }

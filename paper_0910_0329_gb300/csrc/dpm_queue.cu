@@ -360,7 +360,28 @@ __device__ int refill_queue(const QDev &Q, int t, int home, int probes, unsigned
   return n;
 }
 
-// Context of a batch job for the physics (the job table lives in global memory).
+// What a particle step of a batch job reads of its job: the phantom and the
+// history numbering.  A shared launch copies these records of all its jobs
+// into shared memory at the start (64 bytes each, at most kSharedJobs), so
+// that a step reads them from shared memory instead of the job table.
+struct JobHot {
+  DevPhantom P;
+  uint64_t first;
+  uint32_t key0, key1;
+};
+
+struct JobStepCtx {
+  const DevTables &T;
+  const DevPhantom &P;
+  uint64_t first;
+  uint32_t key0, key1;
+};
+
+__device__ __forceinline__ JobStepCtx job_step_ctx(const RunParams &R, const JobHot *sj, int j) {
+  return JobStepCtx{R.T, sj[j].P, sj[j].first, sj[j].key0, sj[j].key1};
+}
+
+// Context of a batch job for the source (the job table lives in global memory).
 __device__ __forceinline__ JobCtx job_ctx(const RunParams &R, int j) {
   const DevJob &J = R.jobs[j];
   return JobCtx{R.T, J.P, J.S, J.first, J.key0, J.key1};
@@ -537,6 +558,16 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
   unsigned sleep_ns = 128;
   unsigned retry_ns = 32;
   const unsigned long long t_start = __shfl_sync(kFull, now_ns(), 0);
+  // batch launches: the jobs' step records in shared memory (all threads of
+  // the block are here, before any divergent code)
+  extern __shared__ JobHot sjobs[];
+  if (kMulti) {
+    for (int j = threadIdx.x; j < R.n_jobs; j += blockDim.x) {
+      const DevJob &J = R.jobs[j];
+      sjobs[j] = JobHot{J.P, J.first, J.key0, J.key1};
+    }
+    __syncthreads();
+  }
   for (;;) {
     unsigned live = __ballot_sync(kFull, alive);
     if (live == 0) mode = -1;
@@ -627,18 +658,18 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
     }
     if (alive) {
       if (mode == 0) {
-        alive = kMulti ? photon_segment(p, job_ctx(R, p.job), sk, DPM_PHOTON_DRAWS)
+        alive = kMulti ? photon_segment(p, job_step_ctx(R, sjobs, p.job), sk, DPM_PHOTON_DRAWS)
                        : photon_segment(p, R, sk, DPM_PHOTON_DRAWS);
         if (alive && ++nstep >= kMaxPhotonSegments * 8) {
           sk.error(ERR_STEPCAP);
-          sk.deposit(kMulti ? vox(p, R.jobs[p.job].P) : vox(p, R.P), p.E);
+          sk.deposit(kMulti ? vox(p, sjobs[p.job].P) : vox(p, R.P), p.E);
           alive = false;
         }
       } else {
-        alive = kMulti ? electron_step(p, job_ctx(R, p.job), sk) : electron_step(p, R, sk);
+        alive = kMulti ? electron_step(p, job_step_ctx(R, sjobs, p.job), sk) : electron_step(p, R, sk);
         if (alive && ++nstep >= kMaxElectronSteps) {
           sk.error(ERR_STEPCAP);
-          sk.deposit(kMulti ? vox(p, R.jobs[p.job].P) : vox(p, R.P), p.E);
+          sk.deposit(kMulti ? vox(p, sjobs[p.job].P) : vox(p, R.P), p.E);
           alive = false;
         }
       }
@@ -665,13 +696,17 @@ const QKernel kQueueKernels[6] = {k_queue<false, false>,      k_queue<false, tru
                                   k_queue<true, true>,        k_queue<false, false, true>, k_queue<false, true, true>};
 
 int queue_blocks_per_sm() {
-  // the kernel keeps no shared memory: give the whole carveout to L1, where
-  // the tables are cached
+  // single runs keep no shared memory: the whole carveout goes to L1, where
+  // the tables are cached; a batch launch keeps its jobs' step records there
+  // (kSharedJobs x 64 bytes per block: 8 blocks with their reserved 1 KB
+  // each need the 64 KB configuration, 28 % of the 228 KB)
   int best = 1 << 30;
   for (QKernel k : kQueueKernels) {
     int per_sm = 0;
-    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kQBlock, 0) != cudaSuccess) {
+    const bool multi = k == kQueueKernels[2] || k == kQueueKernels[3];
+    const size_t smem = multi ? kSharedJobs * sizeof(JobHot) : 0;
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, multi ? 28 : 0);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kQBlock, smem) != cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
@@ -705,6 +740,10 @@ int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batc
                  int sm_count, cudaStream_t st, cudaEvent_t start, std::string &err) {
   if (R.jobs && (R.T.flags & DPM_SAUTER)) {
     err = "the photoelectron angle option (DPM_SAUTER) runs in single runs only";
+    return DPM_EINVAL;
+  }
+  if (R.jobs && (R.n_jobs < 1 || R.n_jobs > kSharedJobs)) {
+    err = "a shared launch takes 1 to kSharedJobs jobs";
     return DPM_EINVAL;
   }
   const size_t cs = size_t(1) << log2cs;
@@ -767,8 +806,9 @@ int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batc
   const bool count = o.count_events != 0;
   const bool sauter = (R.T.flags & DPM_SAUTER) != 0;
   if (R.jobs) {
-    if (count) k_queue<true, true><<<K, kQBlock, 0, st>>>(R, Q);
-    else k_queue<true, false><<<K, kQBlock, 0, st>>>(R, Q);
+    const size_t smem = size_t(R.n_jobs) * sizeof(JobHot);
+    if (count) k_queue<true, true><<<K, kQBlock, smem, st>>>(R, Q);
+    else k_queue<true, false><<<K, kQBlock, smem, st>>>(R, Q);
   } else if (sauter) {
     if (count) k_queue<false, true, true><<<K, kQBlock, 0, st>>>(R, Q);
     else k_queue<false, false, true><<<K, kQBlock, 0, st>>>(R, Q);
@@ -827,7 +867,7 @@ int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_
     err = "the queue kernel takes at most 2^31-1 histories per call";
     return DPM_EINVAL;
   }
-  if (R.jobs && (R.n_jobs < 1 || R.n_jobs > kMaxJobs)) {
+  if (R.jobs && (R.n_jobs < 1 || R.n_jobs > kSharedJobs)) {
     err = "bad job count";
     return DPM_EINVAL;
   }

@@ -27,6 +27,10 @@ void queue_free(QueueState &q);
 // and the context's queue memory allocated for it.
 int queue_prepare(QueueState &q, const dpm_run_opts &o, int sm_count, int &K, int &log2cs, std::string &err);
 
+// Jobs one shared (batch) launch of the queue kernel takes: their step
+// records are kept in shared memory.
+constexpr int kSharedJobs = 64;
+
 // Resident blocks per SM of the queue kernel (occupancy query), or 0 on error.
 int queue_blocks_per_sm();
 // Load the queue kernels on the current device now (they are otherwise
