@@ -121,8 +121,9 @@ typedef struct {
                           The queue kernel always runs blocks of 128 threads (it schedules
                           per warp); its size is set by blocks_per_sm */
     int blocks_per_sm; /* queue kernel: resident blocks per SM (0 = as many as fit, 8) */
-    int queue_log2;    /* queue kernel: log2 of each queue shard's capacity (7..20, 0 = 14) */
-    int refill_min;    /* queue kernel: idle lanes before a warp refills (1..32; 0 = 20 for
+    int queue_log2;    /* queue kernel: log2 of each queue shard's capacity (7..20; 0 = 15 for
+                          an electron-beam dpm_run, 14 otherwise) */
+    int refill_min;    /* queue kernel: idle lanes before a warp refills (1..32; 0 = 24 for
                           photon warps, 12 for electron warps) */
     double timeout_s;  /* bound on any device wait (default 20 s) */
     int physics_flags; /* DPM_NO_HARD: no Moller/bremsstrahlung events; DPM_NO_MSC: no

@@ -16,7 +16,7 @@ import os
 DEFAULT_SPACE = {
     "queue_log2": [12, 13, 14, 15],
     "blocks_per_sm": [4, 6, 8],
-    "refill_min": [0, 8, 16, 24],  # 0: the library's per-type defaults (20 photon, 12 electron lanes)
+    "refill_min": [0, 8, 16, 24],  # 0: the library's per-type defaults (24 photon, 12 electron lanes)
 }
 DEFAULT_START = {"queue_log2": 14, "blocks_per_sm": 8, "refill_min": 0}
 

@@ -63,10 +63,11 @@ constexpr int kQBlock = 128;
 constexpr int kStealProbes = DPM_STEAL_PROBES;
 // Default refill thresholds (idle lanes) of photon and electron warps.  A
 // photon lane's particle is short-lived and starting histories is costly, so
-// photon warps gather more idle lanes per refill (6 MV: +7 % against 8 lanes;
-// 24 lanes measured the same, 32 -2 %).
+// photon warps gather more idle lanes per refill (6 MV, 10^7 histories:
+// 16, 20, 22, 24 and 28 lanes measured 6.65, 6.86, 6.94, 7.01 and 6.99 x 10^8
+// histories/s; electron beams within 0.3 % of each other).
 #ifndef DPM_REFILL_MIN_G
-#define DPM_REFILL_MIN_G 20
+#define DPM_REFILL_MIN_G 24
 #endif
 #ifndef DPM_REFILL_MIN_E
 #define DPM_REFILL_MIN_E 12
@@ -824,6 +825,12 @@ int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batc
   return DPM_OK;
 }
 
+// Default shard capacity: 2^14 slots; 2^15 for a single electron-beam run,
+// whose secondary (photon) phase then starts later and runs longer (20 MeV
+// electrons +2 % on the slab phantom, +1.5 % on the 128^3 blobs; 6 MV photons
+// -0.3 %, so photon beams keep 2^14).
+int default_queue_log2(const RunParams &R) { return (!R.jobs && R.S.particle == 1) ? 15 : 14; }
+
 int queue_prepare(QueueState &q, const dpm_run_opts &o, int sm_count, int &K, int &log2cs, std::string &err) {
   const int per_sm = queue_blocks_per_sm();
   if (per_sm < 1) {
@@ -872,7 +879,9 @@ int queue_run(QueueState &q, const RunParams &R, uint64_t batch_size, const dpm_
     return DPM_EINVAL;
   }
   int K = 0, log2cs = 0;
-  const int rc = queue_prepare(q, o, sm_count, K, log2cs, err);
+  dpm_run_opts oq = o;
+  if (oq.queue_log2 <= 0) oq.queue_log2 = default_queue_log2(R);
+  const int rc = queue_prepare(q, oq, sm_count, K, log2cs, err);
   if (rc) return rc;
   return queue_launch(q.mem, K, log2cs, R, batch_size, o, sm_count, st, start, err);
 }
