@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -158,9 +159,15 @@ def issue_roofline(kernel: str, workload: str, hist_per_s: float):
                     "histories) x histories/s, against 4 issue slots per SM per cycle at the maximum SM clock"}
 
 
-def time_to_target(d, pid, wl, chunk, kernel, target=0.01, max_chunks=200):
-    """Run `chunk` histories at a time until sigma/D at D_max <= target;
-    returns the wall time, histories and chunks (device-checked each chunk)."""
+def time_to_target(d, pid, wl, chunk, kernel, target=0.01, max_chunks=200, adaptive=True, aim=0.97):
+    """Run until sigma/D at D_max <= target, from a fresh tally, checking on
+    the device after each run (dpm_dmax_sigma).  The first run has `chunk`
+    histories.  With `adaptive` each later run is sized from the relative
+    sigma r after n histories, as the request server sizes its rounds: about
+    n (r / target)^2 are needed in all, so the run aims at `aim` times that
+    (a little short, so that a noisy sigma estimate rarely overshoots) minus
+    n, and at least chunk / 8; otherwise every run has `chunk` histories.
+    Returns the wall time, histories and runs."""
     import torch
 
     from paper_0910_0329_gb300 import dpm
@@ -171,15 +178,21 @@ def time_to_target(d, pid, wl, chunk, kernel, target=0.01, max_chunks=200):
     n = 0
     rel = float("inf")
     k = 0
+    m = chunk
     for k in range(1, max_chunks + 1):
-        d.run(pid, wl.source, chunk, wl.seed + 7919, first=n, kernel=kernel)
-        n += chunk
+        d.run(pid, wl.source, m, wl.seed + 7919, first=n, kernel=kernel)
+        n += m
         dose, sig, _ = dpm.dpm_dmax_sigma(d.ctx, [pid])[0]
         rel = sig / dose if dose > 0 else float("inf")
         if rel <= target:
             break
+        m = chunk
+        if adaptive and math.isfinite(rel):
+            m = int(min(max(n * (rel / target) ** 2 * aim - n, chunk / 8), 2 ** 31 - 1))
     return {"wall_s": time.perf_counter() - t0, "histories": n, "chunks": k, "sigma_rel": rel,
-            "target": target, "chunk": chunk}
+            "target": target, "chunk": chunk,
+            "rule": ("adaptive: first run `chunk`, then n (r/target)^2 * %.2f - n (at least chunk/8)" % aim)
+            if adaptive else "fixed chunks"}
 
 
 def max_over_ranks(x, world, local):
@@ -451,11 +464,14 @@ def main():
                               "swept over 16 MiB"},
         "peak_kind": "measured (dpm_diag_l2_peaks, this run)"}
 
-    # time to 1 % sigma at D_max, measured: chunks of the step's histories
-    # with a device-side check of sigma/D at D_max after each (the serving
-    # loop's stop rule), from a fresh tally
+    # time to 1 % sigma at D_max, measured from a fresh tally with a
+    # device-side check of sigma/D at D_max after each run: runs sized from
+    # sigma as the serving loop sizes its rounds, and (for comparison) runs of
+    # the step's histories each
     if not args.no_time_to_target:
         line["time_to_1pct_sigma_at_dmax_measured"] = time_to_target(d, pid, wl, n, kernel)
+        line["time_to_1pct_sigma_at_dmax_measured"]["fixed_chunks"] = time_to_target(d, pid, wl, n, kernel,
+                                                                                    adaptive=False)
 
     if not args.no_e2e:
         line["e2e"] = e2e(args, d, wl, n, kernel, local, rank, world)
