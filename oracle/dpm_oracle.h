@@ -24,9 +24,12 @@
  *
  * Parity pins: every function here is checked in tests/test_oracle_*.py
  * against closed forms, textbook values, identities or brute force.  The
- * coupled dose distribution as a whole has no published values to compare
- * with (the paper's figures are not available): "parity unpinned" for the
- * full dose map beyond energy conservation, symmetry and the component pins.
+ * assembled transport is pinned in its limiting cases (uncollided photon
+ * attenuation, the straight CSDA electron depth-energy profile against an
+ * independent ODE solution), by energy conservation per history, mirror
+ * symmetry, history-split invariance and brute-force plane moments.  No
+ * published coupled dose distribution exists to compare the full transport
+ * with (the paper's figures are not in its text).
  */
 #ifndef DPM_ORACLE_H
 #define DPM_ORACLE_H
