@@ -140,6 +140,14 @@ typedef struct {
                           (about 10 % slower); 0 = those counts read 0.  The energy
                           counters and the tally are the same either way.  The per-history
                           kernels always count. */
+    int refill_pause;  /* queue kernel: a warp with particles whose refill found nothing
+                          waits 128 steps before it tries again (1), or tries on every
+                          step (-1); 0 = automatic: the pause for launches of at most
+                          1.6e7 photon-beam histories or 2e6 electron-beam histories
+                          (a batch launch: its jobs' histories, an electron history
+                          counting 8), where it shortens the end of the launch, and none
+                          above, where it costs about 1.5 %.  Scheduling only: the tally
+                          is the same either way. */
 } dpm_run_opts;
 enum { DPM_NO_HARD = 1, DPM_NO_MSC = 2, DPM_SAUTER = 4 };
 

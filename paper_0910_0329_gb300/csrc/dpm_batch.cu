@@ -51,7 +51,15 @@ int batch_device_work(dpm_ctx *c, const Prepared &b, const RunParams &R, const d
                                  c->stream));
   std::string err;
   int rc;
-  if (!b.tab.empty() && (rc = queue_launch(c->queue.mem, K, log2cs, R, 0, o, c->sm_count, c->stream, nullptr, err)))
+  // the shared launch pauses refills when its jobs' work is short (the solo
+  // launches decide from their own histories)
+  dpm_run_opts os = o;
+  if (os.refill_pause == 0) {
+    double w = 0;
+    for (const DevJob &J : b.tab) w += double(J.n) * (J.S.particle == 0 ? 1.0 : kElectronHistoryWeight);
+    os.refill_pause = w <= kPauseMaxHistories ? 1 : -1;
+  }
+  if (!b.tab.empty() && (rc = queue_launch(c->queue.mem, K, log2cs, R, 0, os, c->sm_count, c->stream, nullptr, err)))
     return ctx_fail(c, rc, err);
   for (size_t j = 0; j < b.solo.size(); ++j)
     if ((rc = queue_launch(c->queue.mem, K, log2cs, b.solo[j], b.solo_bs[j], o, c->sm_count, c->stream, nullptr, err)))

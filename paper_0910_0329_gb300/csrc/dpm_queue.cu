@@ -72,6 +72,20 @@ constexpr int kStealProbes = DPM_STEAL_PROBES;
 #ifndef DPM_REFILL_MIN_E
 #define DPM_REFILL_MIN_E 12
 #endif
+// Refill pause (kernels with kPause): a warp with particles waits this many
+// steps, after a refill that added none, before it tries again.  A failed
+// refill costs several dependent L2 round trips (the home shard, then the
+// steal probes).  Where the queues have run dry, at the end of a launch, the
+// sparse warps that carry the last particles paid that on every step, and
+// the end of a launch took longer than its share of histories: a 6 MV launch
+// of 10^6 histories takes 2.41 ms without the pause and 2.11 ms with it, one
+// of 10^7 1.5 % less time.  In the middle of a long launch the pause costs
+// about 1.5 % (6 MV 5x10^7: +1.5 %; 20 MeV electrons at 10^7: +0.7 to
+// +0.9 %), so a launch takes it when it is short (queue_launch).  Pauses of
+// 8 to 128 steps measured; the longer ones were faster.
+#ifndef DPM_REFILL_COOLDOWN
+#define DPM_REFILL_COOLDOWN 128
+#endif
 // Random draws (two Woodcock flights each) a photon lane makes per warp step:
 // a warp does not wait for its lane with the longest run of virtual flights.
 #ifndef DPM_PHOTON_DRAWS
@@ -541,7 +555,7 @@ __device__ void reduce_counters_q(const long long *cnt, int err, const RunParams
 #ifndef DPM_QUEUE_MIN_BLOCKS
 #define DPM_QUEUE_MIN_BLOCKS 8
 #endif
-template <bool kMulti, bool kCount, bool kSauter = false>
+template <bool kMulti, bool kCount, bool kSauter = false, bool kPause = false>
 __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
     k_queue(const __grid_constant__ RunParams R, const __grid_constant__ QDev Q) {
   const int lane = threadIdx.x & 31;
@@ -569,10 +583,14 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
     }
     __syncthreads();
   }
+  int cool = 0;  // warp-uniform (kPause): steps before a warp with particles tries to refill again
   for (;;) {
     unsigned live = __ballot_sync(kFull, alive);
     if (live == 0) mode = -1;
-    if (live == 0 || 32 - __popc(live) >= Q.refill_min[mode > 0 ? 1 : 0]) {
+    const unsigned live_before = live;
+    if (kPause && live != 0 && cool > 0) {
+      --cool;
+    } else if (live == 0 || 32 - __popc(live) >= Q.refill_min[mode > 0 ? 1 : 0]) {
       const unsigned empty = ~live;
       const bool was_alive = alive;
       const int S = kMulti ? current_source_type(R, Q) : src_type;
@@ -619,6 +637,7 @@ __global__ void __launch_bounds__(kQBlock, DPM_QUEUE_MIN_BLOCKS)
         retry_ns = 32;
         sleep_ns = 128;
       }
+      if (kPause) cool = (live != 0u && live == live_before) ? DPM_REFILL_COOLDOWN : 0;
     }
     if (live == 0) {
       // nothing in the lanes: idle until work appears or the run is over
@@ -690,11 +709,35 @@ __global__ void k_queue_init(uint32_t *seq0, uint32_t *seq1, size_t n, uint32_t 
 
 }  // namespace
 
-// The queue kernel's instantiations: batch launch (kMulti) x event counts,
-// and the single-run ones with the photoelectron angle option.
+// The queue kernel's instantiations: single run or batch launch (kMulti) x
+// event counts x refill pause, and the single runs with the photoelectron
+// angle option.
 using QKernel = void (*)(RunParams, QDev);
-const QKernel kQueueKernels[6] = {k_queue<false, false>,      k_queue<false, true>,      k_queue<true, false>,
-                                  k_queue<true, true>,        k_queue<false, false, true>, k_queue<false, true, true>};
+struct QKernelEntry {
+  QKernel k;
+  bool multi;
+};
+const QKernelEntry kQueueKernels[10] = {
+    {k_queue<false, false>, false},
+    {k_queue<false, true>, false},
+    {k_queue<true, false>, true},
+    {k_queue<true, true>, true},
+    {k_queue<false, false, true>, false},
+    {k_queue<false, true, true>, false},
+    {k_queue<false, false, false, true>, false},
+    {k_queue<false, true, false, true>, false},
+    {k_queue<true, false, false, true>, true},
+    {k_queue<true, true, false, true>, true}};
+
+QKernel queue_kernel(bool multi, bool count, bool sauter, bool pause) {
+  if (sauter) return count ? k_queue<false, true, true> : k_queue<false, false, true>;
+  if (multi) {
+    if (pause) return count ? k_queue<true, true, false, true> : k_queue<true, false, false, true>;
+    return count ? k_queue<true, true> : k_queue<true, false>;
+  }
+  if (pause) return count ? k_queue<false, true, false, true> : k_queue<false, false, false, true>;
+  return count ? k_queue<false, true> : k_queue<false, false>;
+}
 
 int queue_blocks_per_sm() {
   // single runs keep no shared memory: the whole carveout goes to L1, where
@@ -702,9 +745,10 @@ int queue_blocks_per_sm() {
   // (kSharedJobs x 64 bytes per block: 8 blocks with their reserved 1 KB
   // each need the 64 KB configuration, 28 % of the 228 KB)
   int best = 1 << 30;
-  for (QKernel k : kQueueKernels) {
+  for (const QKernelEntry &e : kQueueKernels) {
+    const QKernel k = e.k;
     int per_sm = 0;
-    const bool multi = k == kQueueKernels[2] || k == kQueueKernels[3];
+    const bool multi = e.multi;
     const size_t smem = multi ? kSharedJobs * sizeof(JobHot) : 0;
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, multi ? 28 : 0);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kQBlock, smem) != cudaSuccess) {
@@ -720,7 +764,7 @@ int queue_preload() {
   // cudaFuncGetAttributes loads a kernel under lazy module loading
   cudaFuncAttributes a;
   bool ok = cudaFuncGetAttributes(&a, k_queue_init) == cudaSuccess;
-  for (QKernel k : kQueueKernels) ok = ok && cudaFuncGetAttributes(&a, k) == cudaSuccess;
+  for (const QKernelEntry &e : kQueueKernels) ok = ok && cudaFuncGetAttributes(&a, e.k) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     return 0;
@@ -806,17 +850,14 @@ int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batc
   if (start) cudaEventRecord(start, st);
   const bool count = o.count_events != 0;
   const bool sauter = (R.T.flags & DPM_SAUTER) != 0;
-  if (R.jobs) {
-    const size_t smem = size_t(R.n_jobs) * sizeof(JobHot);
-    if (count) k_queue<true, true><<<K, kQBlock, smem, st>>>(R, Q);
-    else k_queue<true, false><<<K, kQBlock, smem, st>>>(R, Q);
-  } else if (sauter) {
-    if (count) k_queue<false, true, true><<<K, kQBlock, 0, st>>>(R, Q);
-    else k_queue<false, false, true><<<K, kQBlock, 0, st>>>(R, Q);
-  } else {
-    if (count) k_queue<false, true><<<K, kQBlock, 0, st>>>(R, Q);
-    else k_queue<false, false><<<K, kQBlock, 0, st>>>(R, Q);
+  bool pause = o.refill_pause > 0;
+  if (o.refill_pause == 0) {
+    // single run: from its own histories; a batch launch's caller decides
+    const double w = R.S.particle == 0 ? 1.0 : kElectronHistoryWeight;
+    pause = !R.jobs && double(R.n) * w <= kPauseMaxHistories;
   }
+  const size_t smem = R.jobs ? size_t(R.n_jobs) * sizeof(JobHot) : 0;
+  queue_kernel(R.jobs != nullptr, count, sauter, pause)<<<K, kQBlock, smem, st>>>(R, Q);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = cudaGetErrorString(e);

@@ -51,7 +51,7 @@ class dpm_run_opts(C.Structure):
     _fields_ = [("kernel", C.c_int), ("n_batches", C.c_int), ("block_size", C.c_int), ("blocks_per_sm", C.c_int),
                 ("queue_log2", C.c_int), ("refill_min", C.c_int), ("timeout_s", C.c_double),
                 ("physics_flags", C.c_int), ("queue_limit", C.c_int), ("use_graph", C.c_int),
-                ("count_events", C.c_int)]
+                ("count_events", C.c_int), ("refill_pause", C.c_int)]
 
 
 class dpm_job(C.Structure):
@@ -403,9 +403,10 @@ def serve_select(next_n, budget) -> list:
 
 
 def run_opts(kernel=KERNEL_QUEUE, n_batches=0, block_size=0, blocks_per_sm=0, queue_log2=0, refill_min=0,
-             timeout_s=0.0, physics_flags=0, queue_limit=0, use_graph=0, count_events=0) -> dpm_run_opts:
+             timeout_s=0.0, physics_flags=0, queue_limit=0, use_graph=0, count_events=0,
+             refill_pause=0) -> dpm_run_opts:
     return dpm_run_opts(kernel, n_batches, block_size, blocks_per_sm, queue_log2, refill_min, timeout_s,
-                        physics_flags, queue_limit, int(use_graph), int(count_events))
+                        physics_flags, queue_limit, int(use_graph), int(count_events), int(refill_pause))
 
 
 def dpm_run_batch(ctx, jobs, opts: dpm_run_opts | None = None):

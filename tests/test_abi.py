@@ -51,7 +51,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(dpm.dpm_material) == 4 + 4 + 3 * 8 * 8 + 8 + 8
     assert ctypes.sizeof(dpm.dpm_table_params) == 7 * 8 + 8
     assert ctypes.sizeof(dpm.dpm_source) == 8 + 8 + 3 * 8 + 4 * 8
-    assert ctypes.sizeof(dpm.dpm_run_opts) == 6 * 4 + 8 + 4 * 4
+    assert ctypes.sizeof(dpm.dpm_run_opts) == 6 * 4 + 8 + 5 * 4 + 4  # trailing padding to 8
     assert ctypes.sizeof(dpm.dpm_job) == 4 + 4 + ctypes.sizeof(dpm.dpm_source) + 3 * 8
     assert ctypes.sizeof(dpm.dpm_run_stats) == 8 + 2 * 4 + 4 * 8 + 5 * 8 + 2 * 8 + 2 * 8
 

@@ -175,3 +175,26 @@ def test_event_counting_changes_nothing_but_the_counts(make, n):
     for k in ("n_e_steps", "n_g_flights", "n_g_interactions", "n_pushed"):
         assert st1[k] == sth[k] > 0 and st0[k] == 0, k
     assert st1["n_tally_atomics"] > 0 and st0["n_tally_atomics"] == 0
+
+
+@pytest.mark.parametrize("make,n", [(W.c1_photon_wbw, 300_000), (W.c0_electron_wlw, 60_000)], ids=["6mv", "e20"])
+def test_refill_pause_changes_nothing_but_the_schedule(make, n):
+    """The queue kernel with the refill pause, without it and with the
+    automatic choice gives the same tally and energy counters, with and
+    without event counts (the pause only changes when warps look for work)."""
+    wl = make()
+
+    def run(pause, count):
+        with dpm.Dpm(0, W.MATERIALS, wl.params) as d:
+            pid = d.load_phantom(wl.phantom)
+            d.run(pid, wl.source, n, wl.seed, refill_pause=pause, count_events=count)
+            _, _, raw, st = d.read(pid)
+        assert st["error_flags"] == 0
+        return raw, st
+
+    ref, st_ref = run(-1, 0)
+    for pause, count in ((1, 0), (0, 0), (1, 1), (-1, 1)):
+        raw, st = run(pause, count)
+        assert np.array_equal(raw, ref), (pause, count)
+        for k in ("emitted", "escaped", "missed", "deposited", "n_histories"):
+            assert st[k] == st_ref[k], (k, pause, count)
