@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -338,14 +339,29 @@ int dpm_set_stream(dpm_ctx *c, void *s) {
 // largest density of each material (for the photon majorant).
 static int scan_phantom(dpm_ctx *c, const uint8_t *mat, const float *rho, size_t V, int &max_mat,
                         double (&rho_max)[DPM_MAX_MAT]) {
-  max_mat = 0;
-  for (int m = 0; m < DPM_MAX_MAT; ++m) rho_max[m] = 0.0;
+  static_assert((DPM_MAX_MAT & (DPM_MAX_MAT - 1)) == 0, "material mask");
+  // one pass without branches: four partial maxima per material, so that
+  // neighbouring voxels of one material do not wait on each other's store
+  float part[4][DPM_MAX_MAT] = {};
+  unsigned bad = 0;
+  int mm = 0;
   for (size_t v = 0; v < V; ++v) {
-    if (mat[v] >= DPM_MAX_MAT) return fail(c, DPM_EINVAL, "material index >= 16");
-    if (!(rho[v] > 0.f) || !std::isfinite(rho[v])) return fail(c, DPM_EINVAL, "density must be positive and finite");
-    max_mat = std::max(max_mat, int(mat[v]));
-    rho_max[mat[v]] = std::max(rho_max[mat[v]], double(rho[v]));
+    const unsigned m = mat[v];
+    const float r = rho[v];
+    bad |= unsigned(m >= DPM_MAX_MAT) | unsigned(!(r > 0.f && r <= FLT_MAX));  // also NaN and +inf
+    float &a = part[v & 3][m & (DPM_MAX_MAT - 1)];
+    a = std::max(a, r);
+    mm = std::max(mm, int(m));
   }
+  if (bad) {
+    for (size_t v = 0; v < V; ++v) {
+      if (mat[v] >= DPM_MAX_MAT) return fail(c, DPM_EINVAL, "material index >= 16");
+      if (!(rho[v] > 0.f) || !std::isfinite(rho[v])) return fail(c, DPM_EINVAL, "density must be positive and finite");
+    }
+  }
+  max_mat = mm;
+  for (int m = 0; m < DPM_MAX_MAT; ++m)
+    rho_max[m] = double(std::max(std::max(part[0][m], part[1][m]), std::max(part[2][m], part[3][m])));
   return DPM_OK;
 }
 
@@ -710,18 +726,20 @@ static int read_common(dpm_ctx *c, PhantomState *p, const int64_t *s1_host, dpm_
     std::memset(st, 0, sizeof(*st));
     st->n_histories = p->n_total;
     st->n_batches = int32_t(p->b_total);
-    double dep = 0;  // the voxel sum can exceed an int64 of 2^-32 MeV quanta
+    // the voxel sum can exceed an int64 of 2^-32 MeV quanta: summed exactly
+    // in 128 bits, then rounded once
+    __int128 dep = 0;
     if (s1_host) {
-      for (size_t v = 0; v < p->V; ++v) dep += double(s1_host[v]);
+      for (size_t v = 0; v < p->V; ++v) dep += s1_host[v];
     } else {
       std::vector<long long> s1(p->V);
       CUDA_TRY(c, cudaMemcpy(s1.data(), p->d_S1, p->V * sizeof(long long), cudaMemcpyDeviceToHost));
-      for (long long x : s1) dep += double(x);
+      for (long long x : s1) dep += x;
     }
     st->emitted = double((long long)cnt[C_EMIT]) / kCounterScale;
     st->escaped = double((long long)cnt[C_ESC]) / kCounterScale;
     st->missed = double((long long)cnt[C_MISS]) / kCounterScale;
-    st->deposited = dep / kTallyScale;
+    st->deposited = double(dep) / kTallyScale;
     st->n_e_steps = cnt[C_ESTEP];
     st->n_g_flights = cnt[C_GFLIGHT];
     st->n_g_interactions = cnt[C_GINT];
@@ -760,11 +778,11 @@ int dpm_read_dose(dpm_ctx *c, int id, double *dose, double *sigma, int64_t *s1_r
     launch_normalize(p->d_S1, p->d_Q, p->d_rho, p->V, double(p->n_total), double(p->b_total), p->dx * p->dy * p->dz,
                      p->d_dose, p->d_sigma, c->sm_count, c->stream);
     CUDA_TRY(c, cudaGetLastError());
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    if (dose) CUDA_TRY(c, cudaMemcpy(dose, p->d_dose, p->V * sizeof(double), cudaMemcpyDeviceToHost));
-    if (sigma) CUDA_TRY(c, cudaMemcpy(sigma, p->d_sigma, p->V * sizeof(double), cudaMemcpyDeviceToHost));
+    if (dose) CUDA_TRY(c, cudaMemcpyAsync(dose, p->d_dose, p->V * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (sigma) CUDA_TRY(c, cudaMemcpyAsync(sigma, p->d_sigma, p->V * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   }
-  if (s1_raw) CUDA_TRY(c, cudaMemcpy(s1_raw, p->d_S1, p->V * sizeof(long long), cudaMemcpyDeviceToHost));
+  if (s1_raw) CUDA_TRY(c, cudaMemcpyAsync(s1_raw, p->d_S1, p->V * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   int rc = read_common(c, p, s1_raw, st, src);
   if (rc) return rc;
   if (src) c->err = keep;
