@@ -47,6 +47,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not needs_build():
         return LIB
     os.makedirs(OUT, exist_ok=True)
+    # one build at a time (ranks of one job may all ask for it): the others
+    # wait on the lock and then find the library up to date
+    import fcntl
+
+    with open(os.path.join(OUT, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and not needs_build():
+            return LIB
+        return _build(verbose)
+
+
+def _build(verbose: bool) -> str:
     nvcc = _nvcc()
     jobs = []
     for f in CU + CPP:
