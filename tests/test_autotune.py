@@ -3,7 +3,7 @@ from paper_0910_0329_gb300 import autotune
 
 
 def test_coordinate_descent_finds_separable_optimum():
-    target = {"queue_log2": 13, "blocks_per_sm": 6, "refill_min": 16}
+    target = {"queue_log2": 13, "blocks_per_sm": 6, "refill_min": 16, "refill_pause": -1}
     calls = []
 
     def trial(o):
@@ -13,7 +13,7 @@ def test_coordinate_descent_finds_separable_optimum():
     best, t, log = autotune.coordinate_descent(trial, autotune.DEFAULT_SPACE, autotune.DEFAULT_START)
     assert best == target
     assert t == 1.0
-    assert len(calls) == len(log) < 4 * 3 * 3  # fewer trials than the full grid, none repeated
+    assert len(calls) == len(log) < 4 * 3 * 4 * 3  # fewer trials than the full grid, none repeated
 
 
 def test_coordinate_descent_ignores_gains_below_the_noise_floor():
@@ -30,7 +30,7 @@ def test_coordinate_descent_ignores_gains_below_the_noise_floor():
 def test_start_outside_the_space_is_projected():
     space = {"queue_log2": [12, 14], "blocks_per_sm": [6, 8], "refill_min": [8]}
     best, _, log = autotune.coordinate_descent(lambda o: 1.0, space, autotune.DEFAULT_START)
-    assert best == {"queue_log2": 14, "blocks_per_sm": 8, "refill_min": 8}
+    assert best == {"queue_log2": 14, "blocks_per_sm": 8, "refill_min": 8}  # only the space's parameters
     assert all(all(o[k] in space[k] for k in space) for o, _ in log)
 
 
@@ -41,3 +41,29 @@ def test_cache_roundtrip(tmp_path):
     autotune.save(k, {"opts": {"refill_min": 4}}, p)
     autotune.save("other", {"opts": {}}, p)
     assert autotune.load(k, p)["opts"] == {"refill_min": 4}
+
+
+def test_full_length_runs_decide_the_final_choice():
+    start = dict(autotune.DEFAULT_START)
+    best = dict(start, refill_min=16)
+    calls = []
+
+    def full(times):
+        def f(o):
+            calls.append(o)
+            return times[o == best]
+        return f
+
+    # the short trials' winner is 5 % faster on the full runs: it is kept
+    choice, t = autotune.confirm(full({False: 1.0, True: 0.95}), best, start)
+    assert choice == best and t == (1.0, 0.95) and len(calls) == 4
+    # 1 % faster on the full runs: within the noise floor, the defaults stay
+    choice, _ = autotune.confirm(full({False: 1.0, True: 0.99}), best, start)
+    assert choice == start
+    # slower on the full runs (the short trials misled): the defaults stay
+    choice, _ = autotune.confirm(full({False: 1.0, True: 1.04}), best, start)
+    assert choice == start
+    # nothing to confirm when the search kept the defaults
+    calls.clear()
+    choice, t = autotune.confirm(full({False: 1.0, True: 0.5}), dict(start), start)
+    assert choice == start and t is None and calls == []
