@@ -726,16 +726,24 @@ static int read_common(dpm_ctx *c, PhantomState *p, const int64_t *s1_host, dpm_
     std::memset(st, 0, sizeof(*st));
     st->n_histories = p->n_total;
     st->n_batches = int32_t(p->b_total);
-    // the voxel sum can exceed an int64 of 2^-32 MeV quanta: summed exactly
-    // in 128 bits, then rounded once
-    __int128 dep = 0;
-    if (s1_host) {
-      for (size_t v = 0; v < p->V; ++v) dep += s1_host[v];
-    } else {
-      std::vector<long long> s1(p->V);
+    // the voxel sum can exceed an int64 of 2^-32 MeV quanta: summed exactly,
+    // the high (signed) and low 32-bit halves apart, neither of which can
+    // overflow 64 bits below 2^32 voxels (the largest phantom has fewer), then
+    // rounded once
+    std::vector<long long> s1;
+    const int64_t *src = s1_host;
+    if (!src) {
+      s1.resize(p->V);
       CUDA_TRY(c, cudaMemcpy(s1.data(), p->d_S1, p->V * sizeof(long long), cudaMemcpyDeviceToHost));
-      for (long long x : s1) dep += x;
+      src = reinterpret_cast<const int64_t *>(s1.data());
     }
+    int64_t hi = 0;
+    uint64_t lo = 0;
+    for (size_t v = 0; v < p->V; ++v) {
+      hi += src[v] >> 32;  // arithmetic shift: floor(x / 2^32)
+      lo += uint64_t(src[v]) & 0xffffffffull;
+    }
+    const __int128 dep = (__int128)hi * 4294967296 + (__int128)lo;
     st->emitted = double((long long)cnt[C_EMIT]) / kCounterScale;
     st->escaped = double((long long)cnt[C_ESC]) / kCounterScale;
     st->missed = double((long long)cnt[C_MISS]) / kCounterScale;
