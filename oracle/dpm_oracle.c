@@ -582,6 +582,8 @@ static double sample_spectrum(ranecu *r) {
     return t * t;
 }
 
+static void isotropic_direction(ranecu *r, double d[3]);
+
 void or_sample(int which, double a, double b, const or_material *m, uint64_t n, uint64_t seed, double *out) {
     (void)m;
     ranecu r;
@@ -595,6 +597,13 @@ void or_sample(int which, double a, double b, const or_material *m, uint64_t n, 
             case OR_S_MSC: out[i] = sample_msc(a, &r); break;
             case OR_S_SPECTRUM: out[i] = sample_spectrum(&r); break;
             case OR_S_SAUTER: out[i] = sample_sauter(a, &r); break;
+            case OR_S_ISO_X:
+            case OR_S_ISO_Z: {
+                double d[3];
+                isotropic_direction(&r, d);
+                out[i] = which == OR_S_ISO_X ? d[0] : d[2];
+                break;
+            }
             default: out[i] = 0;
         }
     }
@@ -663,6 +672,58 @@ static void rotate(double d[3], double c, double phi) {
     d[0] /= n; d[1] /= n; d[2] /= n;
 }
 
+/* Compton scattering of a photon of energy E into eps E (Sec. 2.1,
+   Klein-Nishina): the photon turns by cos theta = 1 - (1/eps - 1)/kappa at
+   azimuth phi; the electron takes T = E - eps E at the polar angle fixed by
+   momentum conservation, cos theta_e = (E - eps E cos theta)/p_e, on the
+   opposite azimuth.  d_g and d_e start as the photon's direction. */
+static void compton_kinematics(double E, double e, double phi, double d_g[3], double d_e[3], double *Ep,
+                               double *T) {
+    *Ep = e * E;
+    *T = E - *Ep;
+    double cth = 1.0 - (1.0 / e - 1.0) / (E / MC2);
+    double pe = sqrt(*T * (*T + 2.0 * MC2));
+    double ce = (E - *Ep * cth) / pe;
+    rotate(d_e, ce, phi + PI);
+    rotate(d_g, cth, phi);
+}
+
+/* Moller collision of an electron of kinetic energy T giving W to the
+   secondary (Sec. 2.1): both polar angles from the two-body kinematics of a
+   collision with an electron at rest, cos^2 theta = W (T + 2 mc^2) /
+   (T (W + 2 mc^2)) for the secondary and the same with T - W for the
+   primary, on opposite azimuths.  d_p and d_s start as the primary's
+   direction. */
+static void moller_kinematics(double T, double W, double phi, double d_p[3], double d_s[3]) {
+    double Tp = T - W;
+    double cs = sqrt(W * (T + 2.0 * MC2) / (T * (W + 2.0 * MC2)));
+    double cp = sqrt(Tp * (T + 2.0 * MC2) / (T * (Tp + 2.0 * MC2)));
+    rotate(d_s, cs, phi);
+    rotate(d_p, cp, phi + PI);
+}
+
+/* Test hook: one interaction's outgoing particles from an incoming
+   direction d_in, for the conservation-law pins.  which 0: Compton (a = E,
+   b = eps); 1: Moller (a = T, b = W).  out = {E1, d1[3], E2, d2[3]}: the
+   scattered photon then the electron, or the primary then the secondary. */
+void or_kinematics(int which, double a, double b, double phi, const double d_in[3], double out[8]) {
+    double d1[3] = {d_in[0], d_in[1], d_in[2]}, d2[3] = {d_in[0], d_in[1], d_in[2]};
+    if (which == 0) {
+        double Ep, T;
+        compton_kinematics(a, b, phi, d1, d2, &Ep, &T);
+        out[0] = Ep;
+        out[4] = T;
+    } else {
+        moller_kinematics(a, b, phi, d1, d2);
+        out[0] = a - b;
+        out[4] = b;
+    }
+    for (int k = 0; k < 3; k++) {
+        out[1 + k] = d1[k];
+        out[5 + k] = d2[k];
+    }
+}
+
 /* ======================================================================= */
 /* Transport                                                                */
 /* ======================================================================= */
@@ -711,15 +772,20 @@ static void push(tctx *c, const part *q) {
 
 static void escape(tctx *c, double e) { c->h_esc += e; }
 
+/* Isotropic direction: cos theta uniform on [-1, 1], azimuth uniform. */
+static void isotropic_direction(ranecu *r, double d[3]) {
+    double cz = 2.0 * ranecu_next(r) - 1.0, phi = 2.0 * PI * ranecu_next(r);
+    double sz = sqrt(1.0 - cz * cz);
+    d[0] = sz * cos(phi); d[1] = sz * sin(phi); d[2] = cz;
+}
+
 /* Two annihilation photons, isotropic and back to back, at the positron's
    final position. */
 static void annihilate(tctx *c, const part *p) {
     part g = *p;
     g.type = 0;
     g.E = MC2;
-    double cz = 2.0 * ranecu_next(&c->rng) - 1.0, phi = 2.0 * PI * ranecu_next(&c->rng);
-    double sz = sqrt(1.0 - cz * cz);
-    g.d[0] = sz * cos(phi); g.d[1] = sz * sin(phi); g.d[2] = cz;
+    isotropic_direction(&c->rng, g.d);
     push(c, &g);
     g.d[0] = -g.d[0]; g.d[1] = -g.d[1]; g.d[2] = -g.d[2];
     push(c, &g);
@@ -775,17 +841,13 @@ static int transport_photon(tctx *c, part *p, int first_flight_only) {
         double r = ranecu_next(&c->rng) * mut[m];
         if (r < muc[m]) {
             /* Compton: photon keeps eps E, electron gets the rest */
-            double E = p->E, e = sample_kn(E, &c->rng), Ep = e * E, T = E - Ep;
-            double cth = 1.0 - (1.0 / e - 1.0) / (E / MC2);
+            double E = p->E, e = sample_kn(E, &c->rng), Ep, T;
             double phi = 2.0 * PI * ranecu_next(&c->rng);
             part el = *p;
             el.type = 1;
+            compton_kinematics(E, e, phi, p->d, el.d, &Ep, &T);
             el.E = T;
-            double pe = sqrt(T * (T + 2.0 * MC2));
-            double ce = (E - Ep * cth) / pe;
-            rotate(el.d, ce, phi + PI);
             emit_charged(c, &el);
-            rotate(p->d, cth, phi);
             p->E = Ep;
             continue;
         } else if (r < muc[m] + mup[m]) {
@@ -895,14 +957,11 @@ static void transport_electron(tctx *c, part *p) {
             /* Moller: secondary gets W = eps T, primary keeps T - W */
             double e = sample_moller(Tn, pr->wcc, &c->rng), W = e * Tn, Tp = Tn - W;
             double phi = 2.0 * PI * ranecu_next(&c->rng);
-            double cs = sqrt(W * (Tn + 2.0 * MC2) / (Tn * (W + 2.0 * MC2)));
-            double cp = sqrt(Tp * (Tn + 2.0 * MC2) / (Tn * (Tp + 2.0 * MC2)));
             part d = *p;
             d.type = 1;
             d.E = W;
-            rotate(d.d, cs, phi);
+            moller_kinematics(Tn, W, phi, p->d, d.d);
             emit_charged(c, &d);
-            rotate(p->d, cp, phi + PI);
             p->E = Tp;
         } else {
             /* bremsstrahlung photon along the electron direction */

@@ -122,7 +122,15 @@ double or_spectrum_cdf(double E);
 
 /* samplers (n draws into out[], RANECU seeded from seed) ------------------ */
 void or_sample(int which, double a, double b, const or_material *m, uint64_t n, uint64_t seed, double *out);
-enum { OR_S_KN = 0, OR_S_MOLLER = 1, OR_S_BREMS = 2, OR_S_PAIR = 3, OR_S_MSC = 4, OR_S_SPECTRUM = 5, OR_S_SAUTER = 6 };
+enum { OR_S_KN = 0, OR_S_MOLLER = 1, OR_S_BREMS = 2, OR_S_PAIR = 3, OR_S_MSC = 4, OR_S_SPECTRUM = 5, OR_S_SAUTER = 6,
+       OR_S_ISO_X = 7, OR_S_ISO_Z = 8 /* x and z of the annihilation photons' isotropic direction */ };
+
+/* One interaction's outgoing particles from direction d_in (pins of the
+   kinematics by momentum conservation).  which 0: Compton of a photon of
+   energy a into b*a; 1: Moller of an electron of kinetic energy a giving b to
+   the secondary.  out = {E1, d1[3], E2, d2[3]}: scattered photon and
+   electron, or primary and secondary. */
+void or_kinematics(int which, double a, double b, double phi, const double d_in[3], double out[8]);
 
 /* RANECU stream for pins: n uniforms from (s1, s2) */
 void or_ranecu_stream(int32_t s1, int32_t s2, int n, double *out, int32_t *state_out);

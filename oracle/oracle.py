@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _SOURCES = [os.path.join(_HERE, "dpm_oracle.c")]
 
 OR_NO_HARD, OR_NO_MSC, OR_NO_SECONDARY_PHOTONS, OR_SAUTER = 1, 2, 4, 8
-S_KN, S_MOLLER, S_BREMS, S_PAIR, S_MSC, S_SPECTRUM, S_SAUTER = range(7)
+S_KN, S_MOLLER, S_BREMS, S_PAIR, S_MSC, S_SPECTRUM, S_SAUTER, S_ISO_X, S_ISO_Z = range(9)
 
 
 def build(force: bool = False) -> str:
@@ -94,6 +94,8 @@ def lib():
             f.restype = d
         L.or_sample.argtypes = [i, d, d, pm, u64, u64, pd]
         L.or_sample.restype = None
+        L.or_kinematics.argtypes = [i, d, d, d, pd, pd]
+        L.or_kinematics.restype = None
         L.or_ranecu_stream.argtypes = [C.c_int32, C.c_int32, i, pd, C.POINTER(C.c_int32)]
         L.or_ranecu_stream.restype = None
         L.or_run.argtypes = [C.POINTER(PhantomS), pm, i, C.POINTER(Params), C.POINTER(SourceS), u64, u64, u64, pd, pd,
@@ -242,6 +244,15 @@ def uncollided(ph, mats_d, pd, src, n, seed) -> int:
     phs = phantom_struct(ph, keep)
     return int(lib().or_uncollided(C.byref(phs), materials(mats_d), len(mats_d), C.byref(params(pd)),
                                    C.byref(source(src)), n, seed))
+
+
+def kinematics(which, a, b, phi, d_in):
+    """One interaction's outgoing particles (or_kinematics): ((E1, d1), (E2, d2))."""
+    din = np.ascontiguousarray(d_in, dtype=np.float64)
+    out = np.zeros(8)
+    lib().or_kinematics(which, a, b, phi, din.ctypes.data_as(C.POINTER(C.c_double)),
+                        out.ctypes.data_as(C.POINTER(C.c_double)))
+    return (out[0], out[1:4]), (out[4], out[5:8])
 
 
 def sample(which, a=0.0, b=0.0, n=100000, seed=1) -> np.ndarray:

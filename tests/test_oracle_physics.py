@@ -472,3 +472,67 @@ def test_sauter_low_energy_limit_is_the_dipole():
     c = 1 - s
     assert abs(c.mean()) < 0.01
     assert c.var() + c.mean() ** 2 == pytest.approx(0.2, abs=0.005)
+
+
+# --- interaction kinematics: conservation laws (Sec. 2.1) -------------------
+MC2_MEV = 0.51099895
+
+
+def _directions(rng, n):
+    """Random unit vectors plus the poles and near-poles (the rotation's
+    special branch)."""
+    v = rng.normal(size=(n, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    extra = np.array([[0, 0, 1.0], [0, 0, -1.0], [1e-12, 0, 1.0], [0, 1e-11, -1.0], [1.0, 0, 0]])
+    extra /= np.linalg.norm(extra, axis=1)[:, None]
+    return np.vstack([v, extra])
+
+
+def _p(T):
+    return math.sqrt(T * (T + 2.0 * MC2_MEV))
+
+
+@pytest.mark.parametrize("E", [0.06, 0.3, 1.0, 6.0, 20.0])
+def test_compton_conserves_energy_and_momentum(E):
+    """Photon E along d -> photon eps E + electron E - eps E: the photon's
+    momentum E d equals eps E d1 + p_e d2, with the electron on its mass
+    shell; a wrong polar angle, a lost azimuth half-turn or a transposed
+    energy fails it."""
+    rng = np.random.default_rng(1)
+    eps_min = 1.0 / (1.0 + 2.0 * E / MC2_MEV)
+    for d0 in _directions(rng, 20):
+        for eps in (eps_min, 0.5 * (eps_min + 1.0), 0.97):
+            for phi in (0.0, 1.1, 4.0):
+                (Eg, d1), (T, d2) = O.kinematics(0, E, eps, phi, d0)
+                assert Eg == pytest.approx(eps * E, rel=1e-14) and Eg + T == pytest.approx(E, rel=1e-14)
+                assert np.linalg.norm(d1) == pytest.approx(1.0, abs=1e-12)
+                assert np.linalg.norm(d2) == pytest.approx(1.0, abs=1e-12)
+                np.testing.assert_allclose(Eg * d1 + _p(T) * d2, E * d0, atol=1e-10 * E)
+                # the textbook Compton relation between the photon's energies and angle
+                assert Eg == pytest.approx(E / (1.0 + E / MC2_MEV * (1.0 - d0 @ d1)), rel=1e-10)
+
+
+@pytest.mark.parametrize("T", [0.45, 1.0, 5.0, 20.0])
+def test_moller_conserves_energy_and_momentum(T):
+    """Electron T along d -> primary T - W + secondary W off an electron at
+    rest: p(T) d = p(T - W) d1 + p(W) d2."""
+    rng = np.random.default_rng(2)
+    for d0 in _directions(rng, 20):
+        for W in (0.2, 0.3 * T, 0.5 * T):
+            for phi in (0.0, 2.0, 5.5):
+                (Tp, d1), (Ws, d2) = O.kinematics(1, T, W, phi, d0)
+                assert Tp == pytest.approx(T - W, rel=1e-14) and Ws == W
+                np.testing.assert_allclose(_p(Tp) * d1 + _p(W) * d2, _p(T) * d0, atol=1e-10 * _p(T))
+
+
+def test_annihilation_photons_are_isotropic():
+    """The annihilation photons' direction (the first photon; the second is
+    its negative by construction): z and x uniform on [-1, 1] (an isotropic
+    unit vector's components are), by chi-square against the flat density."""
+    n = 400_000
+    for which in (O.S_ISO_Z, O.S_ISO_X):
+        c = O.sample(which, n=n, seed=5)
+        assert np.all(np.abs(c) <= 1.0)
+        counts, _ = np.histogram(c, bins=40, range=(-1.0, 1.0))
+        chi2 = float(np.sum((counts - n / 40) ** 2 / (n / 40)))
+        assert stats.chi2.sf(chi2, 39) > 0.001, (which, chi2)
