@@ -50,6 +50,17 @@ def photons_lung():
     return W.Workload("6mv_wlw_61x61x60", ph, src, 0, 8, wl.params)
 
 
+def photons_blob_oblique():
+    """The serving workload's geometry: 6 MV from gantry 60 degrees, a 2x2 cm
+    field centred on the isocentre in the middle of the first 128^3 blob
+    phantom of 0.3 cm voxels (water/lung/bone densities), so the beam crosses
+    the voxel grid obliquely through mixed tissue."""
+    ph = W.blob_phantom(128, 128, 128, 0.3, 100, name="patient0")
+    X, Y, Z = ph.extent
+    src = W.Source(W.PHOTON, W.SPEC_6MV, 6.0, (X / 2, Y / 2, Z / 2), 100.0, 2.0, 2.0, 60.0)
+    return W.Workload("6mv_field2_g60_blob128", ph, src, 0, 9, dict(W.DEFAULT_PARAMS))
+
+
 # name -> (workload factory, oracle histories, GPU histories)
 CASES = {
     "e20_wlw_61x61x60": (W.c0_electron_wlw, 80000, 800000),
@@ -64,6 +75,7 @@ CASES = {
     # keep the voxel z statistic near its normal limit)
     "paper_e20_wlw_61x61x150": (lambda: W.paper_case(W.ELECTRON, "lung"), 240000, 2400000),
     "paper_6mv_wbw_61x61x150": (lambda: W.paper_case(W.PHOTON, "bone"), 6_000_000, 30_000_000),
+    "6mv_field2_g60_blob128": (photons_blob_oblique, 6_000_000, 30_000_000),
 }
 
 _oracle_cache = {}
