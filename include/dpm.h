@@ -146,8 +146,11 @@ typedef struct {
                           1.6e7 photon-beam histories or 2e6 electron-beam histories
                           (a batch launch: its jobs' histories, an electron history
                           counting 8), where it shortens the end of the launch, and none
-                          above, where it costs about 1.5 %.  Scheduling only: the tally
-                          is the same either way. */
+                          above, where it costs about 1.5 %; none either with queue
+                          shards below 2^13 slots (queue_log2 < 13, or
+                          dpm_run_noalloc's), which need every refill to keep from
+                          overflowing.  Scheduling only: the tally is the same either
+                          way, unless a queue overflows. */
 } dpm_run_opts;
 enum { DPM_NO_HARD = 1, DPM_NO_MSC = 2, DPM_SAUTER = 4 };
 

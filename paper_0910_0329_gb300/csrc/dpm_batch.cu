@@ -57,12 +57,14 @@ int batch_device_work(dpm_ctx *c, const Prepared &b, const RunParams &R, const d
   if (os.refill_pause == 0) {
     double w = 0;
     for (const DevJob &J : b.tab) w += double(J.n) * (J.S.particle == 0 ? 1.0 : kElectronHistoryWeight);
-    os.refill_pause = w <= kPauseMaxHistories ? 1 : -1;
+    os.refill_pause = (w <= kPauseMaxHistories && log2cs >= kPauseMinLog2) ? 1 : -1;
   }
   if (!b.tab.empty() && (rc = queue_launch(c->queue.mem, K, log2cs, R, 0, os, c->sm_count, c->stream, nullptr, err)))
     return ctx_fail(c, rc, err);
+  dpm_run_opts oo = o;  // the solo launches decide by their own length, on large enough queues
+  if (oo.refill_pause == 0 && log2cs < kPauseMinLog2) oo.refill_pause = -1;
   for (size_t j = 0; j < b.solo.size(); ++j)
-    if ((rc = queue_launch(c->queue.mem, K, log2cs, b.solo[j], b.solo_bs[j], o, c->sm_count, c->stream, nullptr, err)))
+    if ((rc = queue_launch(c->queue.mem, K, log2cs, b.solo[j], b.solo_bs[j], oo, c->sm_count, c->stream, nullptr, err)))
       return ctx_fail(c, rc, err);
   for (size_t j = 0; j < b.tab.size(); ++j) {
     PhantomState *p = b.ph[j];

@@ -656,7 +656,11 @@ int dpm_run(dpm_ctx *c, int id, const dpm_source *src, uint64_t first, uint64_t 
                          c->stream);
   } else {
     std::string qerr;
-    int qrc = queue_run(c->queue, R, bs, o, c->sm_count, c->stream, ev[0], qerr);
+    // automatic refill pause only on queues of 2^kPauseMinLog2 slots or more
+    // (the default capacities are; a small queue_log2 needs every refill)
+    dpm_run_opts oq = o;
+    if (oq.refill_pause == 0 && oq.queue_log2 > 0 && oq.queue_log2 < kPauseMinLog2) oq.refill_pause = -1;
+    int qrc = queue_run(c->queue, R, bs, oq, c->sm_count, c->stream, ev[0], qerr);
     if (qrc) return fail(c, qrc, qerr);
   }
   CUDA_TRY(c, cudaGetLastError());

@@ -104,6 +104,7 @@ extern "C" int dpm_run_noalloc(dpm_ctx *c, int phantom_id, const dpm_source *src
   R.err = reinterpret_cast<int *>(hdr + 128);
   dpm_run_opts o{};
   o.count_events = stats ? 1 : 0;
+  o.refill_pause = -1;  // 512-slot shards need every refill (kPauseMinLog2)
   if ((rc = queue_launch(hdr + kHeader, K, kNoAllocLog2Slots, R, n_histories, o, c->sm_count, c->stream, nullptr,
                          err)))
     return ctx_fail(c, rc, err);

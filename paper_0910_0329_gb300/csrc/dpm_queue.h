@@ -39,6 +39,10 @@ constexpr int kSharedJobs = 64;
 // pays below about 2x10^7 photon histories.
 constexpr double kPauseMaxHistories = 1.6e7;
 constexpr double kElectronHistoryWeight = 8.0;
+// ... and only with shards of at least 2^kPauseMinLog2 slots: small queues
+// (the no-allocation entry point's, or a small queue_log2) need every refill
+// to keep the producers' shards from overflowing.
+constexpr int kPauseMinLog2 = 13;
 
 // Resident blocks per SM of the queue kernel (occupancy query), or 0 on error.
 int queue_blocks_per_sm();
