@@ -852,7 +852,8 @@ int queue_launch(void *mem, int K, int log2cs, const RunParams &R, uint64_t batc
   const bool sauter = (R.T.flags & DPM_SAUTER) != 0;
   bool pause = o.refill_pause > 0;
   if (o.refill_pause == 0) {
-    // single run: from its own histories; a batch launch's caller decides
+    // single run: from its own histories (callers on queues below
+    // 2^kPauseMinLog2 slots pass -1); a batch launch's caller decides
     const double w = R.S.particle == 0 ? 1.0 : kElectronHistoryWeight;
     pause = !R.jobs && double(R.n) * w <= kPauseMaxHistories;
   }
