@@ -1,6 +1,7 @@
 """Host logic of bench.py (no GPU): the kernel source fingerprint that ties a
 committed ncu summary to the source it was captured from, and the lookup of
 the summary's per-history traffic, which must refuse a stale capture."""
+import math
 import os
 import shutil
 
@@ -89,3 +90,55 @@ def test_clock_samples_are_summarised():
     assert c.stop()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     c = bench.Clocks(0)  # never started: no nvidia-smi
     assert c.stop()["samples"] == 0
+
+
+class _FakeDpm:
+    """Stand-in for the library in bench.time_to_target: sigma/D at D_max of
+    n histories is r1 / sqrt(n), optionally with a fixed relative bias of the
+    estimate (the batch estimate of sigma is itself uncertain)."""
+
+    def __init__(self, r1, bias=1.0):
+        self.r1, self.bias, self.n, self.runs = r1, bias, 0, []
+        self.ctx = object()
+
+    def run(self, pid, src, n, seed, first=0, kernel=0):
+        assert first == self.n  # consecutive history ranges
+        self.n += n
+        self.runs.append(n)
+
+
+def _patch(monkeypatch, fake):
+    from paper_0910_0329_gb300 import dpm
+
+    monkeypatch.setattr(dpm, "dpm_reset_tally", lambda ctx, pid: None)
+    monkeypatch.setattr(dpm, "dpm_dmax_sigma",
+                        lambda ctx, ids: [(1.0, fake.bias * fake.r1 / fake.n ** 0.5, 0)])
+
+
+@pytest.mark.parametrize("bias", [1.0, 0.95, 1.1])
+def test_time_to_target_sizes_its_runs_from_sigma(monkeypatch, bias):
+    """The stop rule: the first run has the step's histories, the next ones
+    are sized from sigma (n (r/target)^2 * 0.97 - n, at least a step / 8), and
+    it stops at the first check at or below the target: fewer runs than
+    fixed chunks, and at most a top-up more histories."""
+    import types
+
+    torch = types.SimpleNamespace(cuda=types.SimpleNamespace(synchronize=lambda: None))
+    monkeypatch.setitem(__import__("sys").modules, "torch", torch)
+    chunk, r1 = 10_000_000, 100.0  # 1 % at 10^8 histories
+    need = (bias * r1 / 0.01) ** 2  # histories at which the estimate reaches 1 %
+    wl = types.SimpleNamespace(source=None, seed=1)
+
+    fake = _FakeDpm(r1, bias)
+    _patch(monkeypatch, fake)
+    res = bench.time_to_target(fake, 0, wl, chunk, 0)
+    assert res["sigma_rel"] <= 0.01 and res["histories"] == fake.n == sum(fake.runs)
+    assert fake.runs[0] == chunk and all(m >= chunk // 8 for m in fake.runs)
+    # the sized run aims 3 % short; then top-ups of at least chunk / 8
+    assert res["chunks"] <= 2 + math.ceil(0.04 * need / (chunk // 8))
+    assert need * (1 - 1e-9) <= fake.n <= need + chunk // 8
+    fixed = _FakeDpm(r1, bias)
+    _patch(monkeypatch, fixed)
+    res_f = bench.time_to_target(fixed, 0, wl, chunk, 0, adaptive=False)
+    assert all(m == chunk for m in fixed.runs) and res_f["chunks"] == len(fixed.runs)
+    assert res_f["chunks"] > res["chunks"] and fake.n <= fixed.n + chunk // 8
